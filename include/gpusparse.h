@@ -1,0 +1,235 @@
+/*
+ * gpusparse.h -- exact batched sparse scoring on a GPU-resident inverted index
+ * (GB300, sm_103a).  C ABI: plain pointers and sizes, no framework types.
+ *
+ * Problem (Sec. 4.1, Eq. 4-5 of "GPUSparse: GPU-Accelerated Learned Sparse
+ * Retrieval with Parallel Inverted Indices"): for each query q = {(t_i, w_i)}
+ * of a batch and every document d of the collection,
+ *     score(q, d) = sum_i w_i * s_d(t_i),
+ * with s_d(t) the impact the index stores for (d, t) (0 if absent), computed
+ * by scatter-adding every posting of every query term (no pruning, Sec. 4.3);
+ * then the exact top-k of each query under the order (score descending,
+ * document id ascending).  All N documents are eligible, including those that
+ * score 0.
+ *
+ * Index layout (Sec. 3.2, Eq. 2-3): term-major posting lists, each sorted by
+ * document id and padded to a multiple of W = 32 postings with (doc -1,
+ * impact 0).  Every 32-posting block is stored contiguously as
+ * [32 x int32 doc ids][32 x impact], so both halves are 128-bit loadable.
+ *
+ * Conventions for every entry point:
+ *   - "device" pointers must point to memory of the current CUDA device;
+ *     "host" pointers to host memory (pinned for the copies to overlap).
+ *   - stream: a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     asynchronous on it unless stated; inputs must stay valid until the work
+ *     enqueued on the stream has run.
+ *   - the caller owns every input, output and workspace buffer; the library
+ *     owns gs_index objects and never allocates inside gs_search.
+ *   - argument errors are reported synchronously by the return value; data
+ *     errors found on the device (a query term id outside [0, V), a
+ *     non-finite query weight) skip the offending query term and set a flag
+ *     word in the workspace, read with gs_search_flags().
+ *   - no entry point is thread-safe against a concurrent gs_index_free of the
+ *     same index.
+ */
+#ifndef GPUSPARSE_H
+#define GPUSPARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* gs_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, k > N, ... */
+  GS_ERR_OUT_OF_MEMORY = 2, /* index build could not allocate */
+  GS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  GS_ERR_UNSUPPORTED = 4,   /* valid but not supported (k > GS_MAX_K, ...) */
+  GS_ERR_DATA = 5,          /* invalid document data at index build */
+  GS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  GS_ERR_WORKSPACE = 7      /* workspace smaller than gs_search_workspace_size() */
+} gs_status;
+
+/* Stored impact type of the index (the paper stores float32, Sec. 3.2;
+ * reduced precisions follow its future-work item 2, Sec. 7).
+ *   F32  : float32 impacts, float32 accumulation, float32 scores.
+ *   F16  : IEEE binary16 impacts (nearest-even), float32 accumulation.
+ *   BF16 : bfloat16 impacts (nearest-even), float32 accumulation.
+ *   U8   : uint8 impacts round(w * 255 / 5) (nearest-even of 51 w, document
+ *          weights must lie in [0, 5]); query weights are quantised by the
+ *          same rule, clamped to [0, 255]; int32 accumulation and int32 scores
+ *          (exact: a query may hold at most GS_MAX_QUERY_TERMS_U8 terms). */
+typedef enum { GS_IMPACT_F32 = 0, GS_IMPACT_F16 = 1, GS_IMPACT_BF16 = 2, GS_IMPACT_U8 = 3 } gs_impact;
+
+/* Scoring kernels.
+ *   TERM_PARALLEL : the paper's batched scatter-add (Sec. 4.2, 5.2): every
+ *                   (query, term, posting chunk) work item adds its
+ *                   contributions into dense [B x N] score rows with global
+ *                   atomics; then a radix-select top-k over the rows.
+ *   DOC_TILED     : a doc tile of the score rows of a group of queries lives
+ *                   in shared memory; every (term, tile) posting segment is
+ *                   read once per group (the hybrid kernel of Sec. 7, future
+ *                   work 1).  Candidates above a per-query threshold taken
+ *                   from a sampled subset of tiles are kept; the dense rows
+ *                   are never written.
+ *   DOC_PARALLEL  : one thread per (query, document): walks the document's
+ *                   terms against a dense query vector (Sec. 5.3), no atomics.
+ *   AUTO          : DOC_TILED when the index has a tile table, else
+ *                   TERM_PARALLEL. */
+typedef enum {
+  GS_ALGO_AUTO = 0,
+  GS_ALGO_TERM_PARALLEL = 1,
+  GS_ALGO_DOC_TILED = 2,
+  GS_ALGO_DOC_PARALLEL = 3
+} gs_algo;
+
+#define GS_BLOCK 32                  /* W, postings per block (Sec. 3.2, Eq. 2) */
+#define GS_MAX_K 2048                /* largest supported k */
+#define GS_MAX_QUERY_TERMS_U8 33000  /* 255 * 255 * 33000 < 2^31 */
+
+/* flag bits of the workspace flag word */
+#define GS_FLAG_BAD_TERM 1u     /* a query term id outside [0, V) was skipped */
+#define GS_FLAG_BAD_WEIGHT 2u   /* a non-finite query weight was skipped */
+#define GS_FLAG_CAND_OVERFLOW 4u/* doc-tiled: a candidate list overflowed and
+                                   the row was recomputed on the dense path */
+#define GS_FLAG_TIMEOUT 8u      /* a bounded device wait gave up */
+#define GS_FLAG_BAD_INDPTR 16u  /* the query CSR row pointer was not monotone
+                                   or did not end at q_nnz: results undefined */
+
+typedef struct gs_index gs_index;
+
+typedef struct {
+  int32_t tile_docs; /* documents per tile of the segment table used by the
+                        doc-tiled kernel: a power of two in [256, 65536];
+                        0 = default (1024); -1 = build no table */
+  int32_t reserved[7];
+} gs_build_opts;
+
+typedef struct {
+  int64_t num_docs;
+  int64_t postings;         /* non-zeros of the collection */
+  int64_t padded_postings;  /* sum of padded_length(t) (Sec. 3.2, Eq. 2) */
+  int64_t blocks;           /* padded_postings / 32 */
+  int64_t posting_bytes;    /* blocks * block_bytes */
+  int64_t meta_bytes;       /* per-term arrays and the tile segment table */
+  int32_t vocab;
+  int32_t impact;           /* gs_impact */
+  int32_t block_bytes;      /* 256 (F32), 192 (F16/BF16), 160 (U8) */
+  int32_t tile_docs;        /* 0 when no tile table was built */
+  int32_t num_tiles;
+  int32_t score_is_int;     /* 1 on the U8 path: scores are int32 */
+} gs_index_stats;
+
+/* Read-only views of the index's device arrays (for inspection and tests).
+ * block b of term t is b in [term_block[t], term_block[t + 1]).  seg is
+ * [vocab][num_tiles + 1]: seg[t * (num_tiles + 1) + j] is the position
+ * within the list of t of its first posting with doc id >= j * tile_docs. */
+typedef struct {
+  const void* blocks;         /* blocks * block_bytes bytes */
+  const int64_t* term_block;  /* [vocab + 1] */
+  const int32_t* term_len;    /* [vocab] postings of each list, unpadded */
+  const float* max_score;     /* [vocab] largest stored impact of each list */
+  const uint32_t* seg;        /* see above; NULL without a tile table */
+} gs_index_layout;
+
+typedef struct {
+  int32_t algo;          /* gs_algo */
+  int32_t group_queries; /* DOC_TILED: queries per group (0 = auto) */
+  int32_t tile_docs;     /* DOC_TILED: docs per tile, a multiple of the
+                            index's tile_docs (0 = auto) */
+  int32_t chunk_blocks;  /* TERM_PARALLEL: blocks per work item (0 = auto) */
+  int32_t sample_stride; /* DOC_TILED: 1 of every R tiles forms the threshold
+                            sample (0 = auto, 1 = no sampling: every
+                            document is a candidate) */
+  int32_t reserved[3];
+} gs_search_opts;
+
+/* --- index --------------------------------------------------------------- */
+
+/* Builds the index (Sec. 3.2) from documents given as CSR on the device:
+ *   doc_indptr [num_docs + 1] int64, doc_indptr[0] = 0, non-decreasing,
+ *               doc_indptr[num_docs] = nnz;
+ *   doc_terms  [nnz] int32 term ids in [0, vocab), no term twice in a doc;
+ *   doc_w      [nnz] float32 finite weights (U8: in [0, 5]; F16: within the
+ *               binary16 range).
+ * Runs on `stream` and synchronises it before returning.  Returns
+ * GS_ERR_DATA for invalid document data (no index is created),
+ * GS_ERR_OUT_OF_MEMORY when device memory runs out.  *out receives a
+ * library-owned handle, released with gs_index_free. */
+gs_status gs_index_build(const int64_t* doc_indptr, const int32_t* doc_terms, const float* doc_w,
+                         int64_t num_docs, int64_t nnz, int32_t vocab, gs_impact impact,
+                         gs_stream_t stream, gs_index** out);
+
+/* Same with build options (NULL = defaults). */
+gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t* doc_terms, const float* doc_w,
+                            int64_t num_docs, int64_t nnz, int32_t vocab, gs_impact impact,
+                            const gs_build_opts* opts, gs_stream_t stream, gs_index** out);
+
+gs_status gs_index_info(const gs_index* index, gs_index_stats* out);
+gs_status gs_index_get_layout(const gs_index* index, gs_index_layout* out);
+void gs_index_free(gs_index* index);
+
+/* --- search -------------------------------------------------------------- */
+
+/* Device workspace bytes gs_search / gs_score_dense need for a batch of
+ * `batch` queries holding `q_nnz` terms in total, with top-`k` (k is
+ * ignored by gs_score_dense).  opts may be NULL.  host_io != 0 adds room
+ * for gs_search_host's device copies of the queries and results. */
+gs_status gs_search_workspace_size(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
+                                   const gs_search_opts* opts, int32_t host_io, size_t* bytes);
+
+/* Exact top-k of a batch of queries (Sec. 4, Eq. 4-5 + exact top-k).
+ * Queries are CSR on the device:
+ *   q_indptr [batch + 1] int32, q_indptr[0] = 0, non-decreasing,
+ *             q_indptr[batch] = q_nnz;
+ *   q_terms  [q_nnz] int32 term ids; q_w [q_nnz] float32 weights.
+ *   A term may repeat inside a query: every occurrence contributes.
+ * Outputs on the device, row-major [batch x k]:
+ *   out_ids    int32 document ids, ordered by (score desc, id asc);
+ *   out_scores float32 scores (int32 on the U8 path).
+ * 1 <= k <= min(N, GS_MAX_K).  workspace: device, >= the size reported by
+ * gs_search_workspace_size for the same arguments, 256-byte aligned; it is
+ * used as scratch and must not be shared by calls that overlap on the GPU.
+ * Asynchronous on `stream`; never synchronises or allocates. */
+gs_status gs_search(const gs_index* index, const int32_t* q_indptr, const int32_t* q_terms,
+                    const float* q_w, int32_t batch, int64_t q_nnz, int32_t k, int32_t* out_ids,
+                    void* out_scores, void* workspace, size_t workspace_bytes,
+                    const gs_search_opts* opts, gs_stream_t stream);
+
+/* gs_search with the queries and results in host memory: copies the queries
+ * to the workspace, searches, copies the results back and synchronises the
+ * stream before returning.  The workspace must be sized with host_io = 1. */
+gs_status gs_search_host(const gs_index* index, const int32_t* h_q_indptr, const int32_t* h_q_terms,
+                         const float* h_q_w, int32_t batch, int64_t q_nnz, int32_t k,
+                         int32_t* h_out_ids, void* h_out_scores, void* workspace,
+                         size_t workspace_bytes, const gs_search_opts* opts, gs_stream_t stream);
+
+/* The dense score rows of Eq. 4 without top-k: out_rows [batch x num_docs]
+ * on the device, float32 (int32 on the U8 path).  Same query and workspace
+ * conventions as gs_search; the term-parallel scatter-add computes them. */
+gs_status gs_score_dense(const gs_index* index, const int32_t* q_indptr, const int32_t* q_terms,
+                         const float* q_w, int32_t batch, int64_t q_nnz, void* out_rows,
+                         void* workspace, size_t workspace_bytes, gs_stream_t stream);
+
+/* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits the last
+ * call that used `workspace` raised. */
+gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags);
+
+/* --- misc ---------------------------------------------------------------- */
+
+const char* gs_status_str(gs_status status);
+/* the CUDA error string of the last GS_ERR_CUDA on this host thread */
+const char* gs_last_cuda_error(void);
+int32_t gs_version(void); /* major * 10000 + minor * 100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPUSPARSE_H */

@@ -1,0 +1,591 @@
+// Doc-tiled scoring with a sampled threshold (the hybrid kernel the paper
+// proposes as future work 1, Sec. 7: scatter-add work efficiency with
+// shared-memory accumulation), designed for sm_103a.
+//
+// The queries of a batch form groups of G consecutive queries; the documents
+// form tiles of T consecutive ids.  One CTA owns a (group, tile) pair and keeps
+// the G x T block of score rows in shared memory.  For every distinct term of
+// the group it reads the segment of the term's posting list that falls inside
+// the tile (the segment table of the index gives its bounds, lists being
+// doc-sorted, Sec. 3.2) once, 32 postings per warp step, and adds w * x into
+// the rows of every query of the group holding the term (shared-memory
+// reductions, no global atomics).  Padding (doc -1) lies outside every
+// segment.
+//
+// Exact top-k without dense rows: every R-th full tile is a sample tile.  The
+// sample tiles are scored first and written out; the k-th largest sample
+// score theta_q of each query is a lower bound of its k-th largest score over
+// all documents.  The remaining tiles are then scored, and every document
+// with score > theta_q is appended to a per-query candidate list; documents
+// equal to theta_q set a bit in a per-query tie bitmap.  A final kernel per
+// query returns the top-k of the candidates by (score desc, id asc), taking
+// the lowest-id ties when fewer than k candidates exceed theta_q.  Every
+// document's score is computed exactly once, so the bound holds exactly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "gs_doctiled.cuh"
+#include "gs_topk.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kDtThreads = 1024;
+constexpr int kDtMaxAccBytes = 192 * 1024;
+constexpr int kDefaultGroup = 32;
+constexpr int kDefaultSampleStride = 16;
+
+struct DtConfig {
+  int G = 0, T = 0, m = 0, R = 0;  // R = 0: no sampling
+  int ng = 0, nt = 0, n_sample = 0;
+  int64_t sample_docs = 0;
+  int64_t cap = 0;
+  int64_t bm_words = 0;
+};
+
+gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts, DtConfig* c) {
+  if (!ix->seg) return GS_ERR_UNSUPPORTED;
+  c->T = (opts && opts->tile_docs > 0) ? opts->tile_docs : ix->tile_docs;
+  if (c->T % ix->tile_docs != 0) return GS_ERR_INVALID_ARG;
+  c->m = c->T / ix->tile_docs;
+  int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
+  G = std::min(G, B);
+  if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {
+    if (opts && opts->group_queries > 0) return GS_ERR_INVALID_ARG;
+    G = std::max(1, kDtMaxAccBytes / (c->T * 4));
+  }
+  c->G = G;
+  c->ng = (B + G - 1) / G;
+  c->nt = (int)((ix->N + c->T - 1) / c->T);
+  const int nt_full = (int)(ix->N / c->T);
+  int R = (opts && opts->sample_stride > 0) ? opts->sample_stride : kDefaultSampleStride;
+  if (opts && opts->sample_stride == 1) R = 0;  // caller asked for no sampling
+  // the sample must hold at least 2k documents
+  while (R > 1 && (int64_t)((nt_full + R - 1) / R) * c->T < 2 * (int64_t)k) R /= 2;
+  if (R >= 1 && (int64_t)((nt_full + R - 1) / R) * c->T < (int64_t)k) R = 0;
+  if (R == 1 && nt_full == c->nt) R = 0;  // everything would be sample: score once, no threshold
+  c->R = R;
+  c->n_sample = R > 0 ? (nt_full + R - 1) / R : 0;
+  c->sample_docs = (int64_t)c->n_sample * c->T;
+  const int64_t n_round = (ix->N + 255) / 256 * 256;
+  c->cap = R > 0 ? std::min<int64_t>(n_round, (4 * (int64_t)k * R + 4096 + 255) / 256 * 256) : n_round;
+  c->bm_words = (ix->N + 31) / 32;
+  return GS_OK;
+}
+
+struct DtPlan {
+  uint32_t* cnt;      // [ng][V]
+  int32_t* u_terms;   // group g at q_indptr[gG]
+  int32_t* u_ptr;     // group g at q_indptr[gG] + g
+  int32_t* n_u;       // [ng]
+  uint2* ent;         // [q_nnz] (query within group, weight bits)
+  uint32_t* samp;     // [B][sample_docs]
+  int32_t* samp_ids;  // [B][k]
+  uint32_t* samp_sc;  // [B][k]
+  uint2* cand;        // [B][cap] (key, doc)
+  uint32_t* cand_cnt; // [B]
+  uint32_t* tiebm;    // [B][bm_words]
+};
+
+DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const DtConfig& c, size_t* bytes) {
+  Carver cv(ws);
+  DtPlan p{};
+  p.cnt = cv.take<uint32_t>((size_t)c.ng * ix->V);
+  p.u_terms = cv.take<int32_t>(q_nnz + 1);
+  p.u_ptr = cv.take<int32_t>(q_nnz + c.ng + 1);
+  p.n_u = cv.take<int32_t>(c.ng);
+  p.ent = cv.take<uint2>(q_nnz + 1);
+  p.samp = cv.take<uint32_t>((size_t)B * std::max<int64_t>(c.sample_docs, 1));
+  p.samp_ids = cv.take<int32_t>((size_t)B * k);
+  p.samp_sc = cv.take<uint32_t>((size_t)B * k);
+  p.cand = cv.take<uint2>((size_t)B * c.cap);
+  p.cand_cnt = cv.take<uint32_t>(B);
+  p.tiebm = cv.take<uint32_t>((size_t)B * c.bm_words);
+  *bytes = cv.size();
+  return p;
+}
+
+__device__ __forceinline__ int ub_i32(const int32_t* a, int n, int32_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// One CTA per group: distinct terms of the group (in term order) and, per
+// term, the (query-in-group, weight) entries; invalid pairs are skipped.
+__global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict__ q_indptr,
+                                                       const int32_t* __restrict__ q_terms,
+                                                       const float* __restrict__ q_w, int32_t B, int32_t q_nnz,
+                                                       int G, int32_t V,
+                                                       int impact, uint32_t* __restrict__ cnt_all,
+                                                       int32_t* __restrict__ u_terms, int32_t* __restrict__ u_ptr,
+                                                       int32_t* __restrict__ n_u, uint2* __restrict__ ent,
+                                                       uint32_t* flags) {
+  __shared__ int warp_buf[32];
+  const int g = blockIdx.x;
+  const int q0 = g * G, q1 = min(B, q0 + G);
+  uint32_t fl = 0;
+  // the query CSR is device data: check it, and keep every access in bounds
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    if (q_indptr[q + 1] < q_indptr[q]) fl |= GS_FLAG_BAD_INDPTR;
+  }
+  if (threadIdx.x == 0 && (q_indptr[0] != 0 || q_indptr[B] != q_nnz)) fl |= GS_FLAG_BAD_INDPTR;
+  const int32_t e0 = min(max(q_indptr[q0], 0), q_nnz);
+  const int32_t e1 = min(max(q_indptr[q1], e0), q_nnz);
+  uint32_t* cnt = cnt_all + (int64_t)g * V;
+  for (int t = threadIdx.x; t < V; t += blockDim.x) cnt[t] = 0u;
+  __syncthreads();
+  for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int32_t t = q_terms[e];
+    const float w = q_w[e];
+    if (t < 0 || t >= V) { fl |= kFlagBadTerm; continue; }
+    if (!isfinite(w)) { fl |= kFlagBadWeight; continue; }
+    atomicAdd(&cnt[t], 1u);
+  }
+  __syncthreads();
+  // distinct terms in increasing id; entry offsets
+  int carry_u = 0, carry_e = 0;
+  const int ubase = e0, pbase = e0 + g;
+  for (int t0 = 0; t0 < V; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    const int c = (t < V) ? (int)__ldcg(&cnt[t]) : 0;
+    int tot_u, tot_e;
+    const int xu = block_excl_scan(c > 0 ? 1 : 0, warp_buf, &tot_u);
+    const int xe = block_excl_scan(c, warp_buf, &tot_e);
+    if (c > 0) {
+      u_terms[ubase + carry_u + xu] = t;
+      u_ptr[pbase + carry_u + xu] = e0 + carry_e + xe;
+      cnt[t] = (uint32_t)(e0 + carry_e + xe);  // fill position
+    }
+    carry_u += tot_u;
+    carry_e += tot_e;
+  }
+  if (threadIdx.x == 0) {
+    n_u[g] = carry_u;
+    u_ptr[pbase + carry_u] = e0 + carry_e;
+  }
+  __syncthreads();
+  for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int32_t t = q_terms[e];
+    const float w = q_w[e];
+    if (t < 0 || t >= V || !isfinite(w)) continue;
+    const int ql = min(max(ub_i32(q_indptr + q0, q1 - q0 + 1, e) - 1, 0), q1 - q0 - 1);
+    const uint32_t pos = atomicAdd(&cnt[t], 1u);
+    const uint32_t wb = impact == GS_IMPACT_U8 ? (uint32_t)quant_u8(w) : __float_as_uint(w);
+    ent[pos] = make_uint2((uint32_t)ql, wb);
+  }
+  if (fl) atomicOr(flags, fl);
+}
+
+template <int IMPACT>
+__device__ __forceinline__ float load_x(const uint8_t* blk, int lane) {
+  if (IMPACT == GS_IMPACT_F32) return __ldg(reinterpret_cast<const float*>(blk + 128) + lane);
+  if (IMPACT == GS_IMPACT_F16) return __half2float(__ldg(reinterpret_cast<const __half*>(blk + 128) + lane));
+  if (IMPACT == GS_IMPACT_BF16)
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(blk + 128) + lane));
+  return (float)__ldg(blk + 128 + lane);
+}
+
+enum { kModeSample = 0, kModeMain = 1 };
+
+// theta_q: key of the k-th largest sample score (stored as raw score bits)
+template <typename AccT>
+__device__ __forceinline__ uint32_t theta_key(const uint32_t* samp_sc, int64_t q, int k, int R) {
+  if (R <= 0) return 0u;  // no sampling: every document is a candidate
+  const uint32_t raw = __ldg(samp_sc + q * k + (k - 1));
+  if (std::is_same<AccT, float>::value) return score_key(__uint_as_float(raw));
+  return score_key((int32_t)raw);
+}
+
+// One CTA per (tile, group): G x T score block in shared memory.
+template <int IMPACT, int MODE>
+__global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
+    const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const uint32_t* __restrict__ seg,
+    int seg_tiles, int64_t N, const int32_t* __restrict__ q_indptr, int32_t B, int32_t q_nnz, int G, int T,
+    int m, int R,
+    int ng, int n_sample, const int32_t* __restrict__ u_terms, const int32_t* __restrict__ u_ptr,
+    const int32_t* __restrict__ n_u, const uint2* __restrict__ ent, uint32_t* __restrict__ samp,
+    int64_t sample_docs, const uint32_t* __restrict__ samp_sc, int k, uint2* __restrict__ cand,
+    uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words) {
+  using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
+  constexpr int bb = block_bytes(IMPACT);
+  extern __shared__ __align__(16) uint8_t dyn_smem[];
+  AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
+  __shared__ uint32_t s_start[kDtThreads], s_end[kDtThreads];
+  __shared__ int32_t s_item[kDtThreads + 1];
+  __shared__ int64_t s_blk0[kDtThreads];
+  __shared__ int32_t s_e0[kDtThreads], s_e1[kDtThreads];
+  __shared__ int warp_buf[32];
+
+  const int g = blockIdx.x % ng;
+  const int tile_idx = blockIdx.x / ng;
+  int tau;
+  if (MODE == kModeSample) {
+    tau = tile_idx * R;
+  } else {
+    tau = tile_idx;
+    if (R > 0 && (tau % R) == 0 && tau / R < n_sample) return;  // a sample tile: already scored
+  }
+  const int q0 = g * G;
+  const int gq = min(G, B - q0);
+  const int64_t doc0 = (int64_t)tau * T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (int i = threadIdx.x; i < G * T; i += blockDim.x) acc[i] = (AccT)0;
+
+  const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
+  const int nterm = n_u[g];
+  const int32_t* ut = u_terms + ebase;
+  const int32_t* up = u_ptr + ebase + g;
+  const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
+  __syncthreads();
+
+  for (int j0 = 0; j0 < nterm; j0 += kDtThreads) {
+    const int j = j0 + threadIdx.x;
+    int items = 0;
+    if (j < nterm) {
+      const int32_t t = ut[j];
+      const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
+      const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
+      s_start[threadIdx.x] = s;
+      s_end[threadIdx.x] = e;
+      s_blk0[threadIdx.x] = __ldg(term_block + t) + (s >> 5);
+      s_e0[threadIdx.x] = __ldg(up + j);
+      s_e1[threadIdx.x] = __ldg(up + j + 1);
+      if (e > s) items = (int)(((e - 1) >> 5) - (s >> 5) + 1);
+    }
+    int total;
+    const int xi = block_excl_scan(items, warp_buf, &total);
+    s_item[threadIdx.x] = xi;
+    if (threadIdx.x == 0) s_item[kDtThreads] = total;
+    const int nloc = min(kDtThreads, nterm - j0);
+    __syncthreads();
+    for (int it = warp; it < total; it += kDtThreads / 32) {
+      const int jj = ub_i32(s_item, nloc, it) - 1;
+      const int b = it - s_item[jj];
+      const uint32_t s = s_start[jj], e = s_end[jj];
+      const uint32_t pos = ((s >> 5) + (uint32_t)b) * 32u + (uint32_t)lane;
+      const bool valid = pos >= s && pos < e;
+      const uint8_t* blk = blocks + (s_blk0[jj] + b) * bb;
+      const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
+      const int dl = (int)(doc - doc0);
+      const int32_t eb = s_e0[jj], ee = s_e1[jj];
+      if (IMPACT == GS_IMPACT_U8) {
+        const int x = (int)__ldg(blk + 128 + lane);
+        for (int32_t en = eb; en < ee; ++en) {
+          const uint2 E = __ldg(ent + en);
+          if (valid) atomicAdd(reinterpret_cast<int32_t*>(acc) + E.x * T + dl, (int32_t)E.y * x);
+        }
+      } else {
+        const float x = load_x<IMPACT>(blk, lane);
+        for (int32_t en = eb; en < ee; ++en) {
+          const uint2 E = __ldg(ent + en);
+          if (valid) atomicAdd(reinterpret_cast<float*>(acc) + E.x * T + dl, __uint_as_float(E.y) * x);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (MODE == kModeSample) {
+    // dense sample rows: samp[q][tile_idx * T + d]
+    for (int i = threadIdx.x; i < gq * T; i += blockDim.x) {
+      const int ql = i / T, d = i - ql * T;
+      const AccT v = acc[ql * T + d];
+      uint32_t bits;
+      memcpy(&bits, &v, 4);
+      samp[(int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d] = bits;
+    }
+  } else {
+    // candidates above theta_q, ties in the bitmap
+    for (int c0 = warp * 32; c0 < gq * T; c0 += kDtThreads) {
+      const int i = c0 + lane;
+      const int ql = i / T, d = i - ql * T;  // T is a multiple of 32: one row per warp step
+      const int q = q0 + ql;
+      const int64_t doc = doc0 + d;
+      const uint32_t theta = theta_key<AccT>(samp_sc, q, k, R);
+      const uint32_t key = score_key(acc[ql * T + d]);
+      const bool in = doc < N;
+      const bool gt = in && key > theta;
+      const bool tie = in && key == theta;
+      const unsigned mgt = __ballot_sync(0xffffffffu, gt);
+      const unsigned mtie = __ballot_sync(0xffffffffu, tie);
+      if (doc0 + (c0 - ql * T) < N && lane == 0) tiebm[(int64_t)q * bm_words + ((doc0 + (c0 - ql * T)) >> 5)] = mtie;
+      if (mgt) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)__popc(mgt));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (gt) {
+          const uint32_t slot = base + (uint32_t)__popc(mgt & ((1u << lane) - 1u));
+          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(key, (uint32_t)doc);
+        }
+      }
+    }
+  }
+}
+
+// Candidates of the sample tiles (their scores sit in the sample rows).
+template <typename ST>
+__global__ void dt_sample_emit_kernel(const uint32_t* __restrict__ samp, int64_t sample_docs, int T, int R,
+                                      const uint32_t* __restrict__ samp_sc, int k, uint2* __restrict__ cand,
+                                      uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm,
+                                      int64_t bm_words) {
+  const int q = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const uint32_t theta = theta_key<ST>(samp_sc, q, k, R);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // uniform per warp: chunks of 32 consecutive sample positions
+  for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < sample_docs; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const int64_t st = i / T;
+    const int64_t doc = st * R * T + (i - st * T);
+    const uint32_t raw = samp[(int64_t)q * sample_docs + i];
+    ST v;
+    memcpy(&v, &raw, 4);
+    const uint32_t key = score_key(v);
+    const bool gt = key > theta, tie = key == theta;
+    const unsigned mgt = __ballot_sync(0xffffffffu, gt);
+    const unsigned mtie = __ballot_sync(0xffffffffu, tie);
+    if (lane == 0) tiebm[(int64_t)q * bm_words + (doc >> 5)] = mtie;
+    if (mgt) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)__popc(mgt));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (gt) {
+        const uint32_t slot = base + (uint32_t)__popc(mgt & ((1u << lane) - 1u));
+        if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(key, (uint32_t)doc);
+      }
+    }
+  }
+}
+
+// Final exact top-k of each query from its candidates (and ties).
+template <typename ST>
+__global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict__ cand,
+                                                        const uint32_t* __restrict__ cand_cnt, int64_t cap,
+                                                        const uint32_t* __restrict__ tiebm, int64_t bm_words,
+                                                        int64_t N, const uint32_t* __restrict__ samp_sc, int R,
+                                                        int k, int32_t* __restrict__ out_ids,
+                                                        ST* __restrict__ out_scores, uint32_t* flags) {
+  __shared__ uint32_t hist[2048];
+  __shared__ uint32_t ck[GS_MAX_K];
+  __shared__ int32_t cid[GS_MAX_K];
+  __shared__ int warp_buf[32];
+  __shared__ uint32_t s_digit;
+  __shared__ int s_need;
+  __shared__ int s_fill;
+  const int q = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const uint32_t raw = cand_cnt[q];
+  if (raw > cap && threadIdx.x == 0) atomicOr(flags, kFlagCandOverflow);
+  const int64_t n = min((int64_t)raw, cap);
+  const uint2* c = cand + (int64_t)q * cap;
+  if (threadIdx.x == 0) s_fill = 0;
+  __syncthreads();
+  if (n >= k) {
+    // radix select on the composite key (key << 32) | ~id: all distinct
+    uint64_t prefix = 0, pmask = 0;
+    int need = k;
+    int shift = 64;
+    bool done = false;
+    while (!done && shift > 0) {
+      const int bits = shift >= 11 ? 11 : shift;
+      shift -= bits;
+      const int nb = 1 << bits;
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      const int64_t iters = (n + blockDim.x - 1) / blockDim.x;
+      for (int64_t itn = 0; itn < iters; ++itn) {
+        const int64_t i = itn * blockDim.x + threadIdx.x;
+        int bin = -1;
+        if (i < n) {
+          const uint2 v = c[i];
+          const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
+          if ((K & pmask) == prefix) bin = (int)((K >> shift) & (uint64_t)(nb - 1));
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+      }
+      __syncthreads();
+      // digit: walk bins from the top (nb <= 2048, two per thread)
+      const int per = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
+      int local = 0;
+      for (int u = 0; u < per; ++u) {
+        const int b = nb - 1 - ((int)threadIdx.x * per + u);
+        if (b >= 0) local += (int)hist[b];
+      }
+      int tot;
+      int acc = block_excl_scan(local, warp_buf, &tot);
+      for (int u = 0; u < per; ++u) {
+        const int b = nb - 1 - ((int)threadIdx.x * per + u);
+        if (b < 0) break;
+        const int h = (int)hist[b];
+        if (acc < need && need <= acc + h) {
+          s_digit = (uint32_t)b;
+          s_need = need - acc;
+        }
+        acc += h;
+      }
+      __syncthreads();
+      const uint32_t D = s_digit;
+      const int new_need = s_need;
+      __syncthreads();
+      prefix |= (uint64_t)D << shift;
+      pmask |= (uint64_t)(nb - 1) << shift;
+      // every key in bin D is taken: stop refining
+      if (new_need == (int)hist[D]) done = true;
+      need = new_need;
+      __syncthreads();
+    }
+    // take every candidate whose composite key, truncated to the resolved
+    // bits, is >= prefix: exactly k of them
+    const int64_t iters = (n + blockDim.x - 1) / blockDim.x;
+    for (int64_t itn = 0; itn < iters; ++itn) {
+      const int64_t i = itn * blockDim.x + threadIdx.x;
+      if (i < n) {
+        const uint2 v = c[i];
+        const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
+        if ((K & pmask) >= prefix) {
+          const int slot = atomicAdd(&s_fill, 1);
+          if (slot < k) {
+            ck[slot] = v.x;
+            cid[slot] = (int32_t)v.y;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  } else {
+    // all candidates, then the lowest-id ties at theta_q
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      ck[i] = c[i].x;
+      cid[i] = (int32_t)c[i].y;
+    }
+    const uint32_t theta = theta_key<ST>(samp_sc, q, k, R);
+    const int need_t = k - (int)n;
+    int taken = 0;
+    const uint32_t* bm = tiebm + (int64_t)q * bm_words;
+    for (int64_t w0 = 0; w0 < bm_words && taken < need_t; w0 += blockDim.x) {
+      const int64_t w = w0 + threadIdx.x;
+      const uint32_t word = w < bm_words ? bm[w] : 0u;
+      int tot;
+      const int before = taken + block_excl_scan(__popc(word), warp_buf, &tot);
+      uint32_t rem = word;
+      int r = before;
+      while (rem && r < need_t) {
+        const int bit = __ffs(rem) - 1;
+        rem &= rem - 1;
+        const int64_t doc = w * 32 + bit;
+        if (doc < N) {
+          ck[n + r] = theta;
+          cid[n + r] = (int32_t)doc;
+        }
+        ++r;
+      }
+      taken += tot;
+    }
+    __syncthreads();
+  }
+  int n_pad = 1;
+  while (n_pad < k) n_pad <<= 1;
+  for (int i = k + threadIdx.x; i < n_pad; i += blockDim.x) {
+    ck[i] = 0u;
+    cid[i] = 0x7fffffff;
+  }
+  bitonic_sort_desc(ck, cid, n_pad);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    out_ids[(int64_t)q * k + j] = cid[j];
+    out_scores[(int64_t)q * k + j] = key_to_score<ST>(ck[j]);
+  }
+}
+
+template <int IMPACT>
+gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
+                       const DtPlan& p, cudaStream_t s) {
+  const size_t smem = (size_t)c.G * c.T * 4;
+  auto ks = dt_tile_kernel<IMPACT, kModeSample>;
+  auto km = dt_tile_kernel<IMPACT, kModeMain>;
+  GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GS_CUDA_TRY(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (c.R > 0) {
+    ks<<<c.n_sample * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N,
+                                                   q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample,
+                                                   p.u_terms,
+                                                   p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.samp_sc, k,
+                                                   p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words);
+    GS_LAUNCH_CHECK();
+    if (IMPACT == GS_IMPACT_U8)
+      topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.samp),
+                                                                c.sample_docs, c.sample_docs, k, p.samp_ids,
+                                                                reinterpret_cast<int32_t*>(p.samp_sc));
+    else
+      topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const float*>(p.samp),
+                                                              c.sample_docs, c.sample_docs, k, p.samp_ids,
+                                                              reinterpret_cast<float*>(p.samp_sc));
+    GS_LAUNCH_CHECK();
+  }
+  km<<<c.nt * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B,
+                                           q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent,
+                                           p.samp, c.sample_docs, p.samp_sc, k, p.cand, p.cand_cnt, c.cap,
+                                           p.tiebm, c.bm_words);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+}  // namespace
+
+gs_status dt_workspace_bytes(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k, const gs_search_opts* opts,
+                             size_t* bytes) {
+  DtConfig c;
+  gs_status st = dt_config(ix, B, k, opts, &c);
+  if (st != GS_OK) return st;
+  carve_dt(nullptr, ix, B, q_nnz, k, c, bytes);
+  return GS_OK;
+}
+
+gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* q_terms, const float* q_w,
+                    int32_t B, int64_t q_nnz, int32_t k, int32_t* out_ids, void* out_scores, void* ws,
+                    size_t ws_bytes, uint32_t* flags, const gs_search_opts* opts, cudaStream_t s) {
+  DtConfig c;
+  gs_status st = dt_config(ix, B, k, opts, &c);
+  if (st != GS_OK) return st;
+  size_t need = 0;
+  DtPlan p = carve_dt(ws, ix, B, q_nnz, k, c, &need);
+  if (need > ws_bytes) return GS_ERR_WORKSPACE;
+  dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt, p.u_terms, p.u_ptr,
+                                       p.n_u, p.ent, flags);
+  GS_LAUNCH_CHECK();
+  GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
+  switch (ix->impact) {
+    case GS_IMPACT_F32: st = launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
+    case GS_IMPACT_F16: st = launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
+    case GS_IMPACT_BF16: st = launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
+    default: st = launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
+  }
+  if (st != GS_OK) return st;
+  if (c.R > 0) {
+    dim3 grid((unsigned)std::min<int64_t>((c.sample_docs + 255) / 256, 64), (unsigned)B);
+    if (ix->impact == GS_IMPACT_U8)
+      dt_sample_emit_kernel<int32_t><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.samp_sc, k, p.cand,
+                                                          p.cand_cnt, c.cap, p.tiebm, c.bm_words);
+    else
+      dt_sample_emit_kernel<float><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.samp_sc, k, p.cand,
+                                                        p.cand_cnt, c.cap, p.tiebm, c.bm_words);
+    GS_LAUNCH_CHECK();
+  }
+  if (ix->impact == GS_IMPACT_U8)
+    dt_final_kernel<int32_t><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.samp_sc,
+                                                c.R, k, out_ids, static_cast<int32_t*>(out_scores), flags);
+  else
+    dt_final_kernel<float><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.samp_sc,
+                                              c.R, k, out_ids, static_cast<float*>(out_scores), flags);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,284 @@
+"""Thin Python binding of libgpusparse (include/gpusparse.h) over ctypes.
+
+Argument marshalling only: every step of index build and search runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  The
+names mirror the C entry points; `Index` is a small convenience owner of a
+gs_index handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpusparse.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OUT_OF_MEMORY, GS_ERR_CUDA = 0, 1, 2, 3
+GS_ERR_UNSUPPORTED, GS_ERR_DATA, GS_ERR_TIMEOUT, GS_ERR_WORKSPACE = 4, 5, 6, 7
+IMPACTS = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3}
+ALGOS = {"auto": 0, "term_parallel": 1, "doc_tiled": 2, "doc_parallel": 3}
+GS_FLAG_BAD_TERM, GS_FLAG_BAD_WEIGHT, GS_FLAG_CAND_OVERFLOW = 1, 2, 4
+GS_FLAG_TIMEOUT, GS_FLAG_BAD_INDPTR = 8, 16
+GS_MAX_K = 2048
+
+EXPORTED = (
+    "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
+    "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
+    "gs_status_str", "gs_last_cuda_error", "gs_version",
+)
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = _lib
+        msg = lib.gs_status_str(status).decode() if lib is not None else str(status)
+        if status == GS_ERR_CUDA and lib is not None:
+            msg += f" ({lib.gs_last_cuda_error().decode()})"
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+class gs_build_opts(ctypes.Structure):
+    _fields_ = [("tile_docs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class gs_index_stats(ctypes.Structure):
+    _fields_ = [("num_docs", ctypes.c_int64), ("postings", ctypes.c_int64), ("padded_postings", ctypes.c_int64),
+                ("blocks", ctypes.c_int64), ("posting_bytes", ctypes.c_int64), ("meta_bytes", ctypes.c_int64),
+                ("vocab", ctypes.c_int32), ("impact", ctypes.c_int32), ("block_bytes", ctypes.c_int32),
+                ("tile_docs", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("score_is_int", ctypes.c_int32)]
+
+
+class gs_index_layout(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_void_p), ("term_block", ctypes.c_void_p), ("term_len", ctypes.c_void_p),
+                ("max_score", ctypes.c_void_p), ("seg", ctypes.c_void_p)]
+
+
+class gs_search_opts(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
+                ("chunk_blocks", ctypes.c_int32), ("sample_stride", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; fails loudly when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2606_26441_gb300._build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    L.gs_index_build.argtypes = [P, P, P, I64, I64, I32, ctypes.c_int, P, ctypes.POINTER(P)]
+    L.gs_index_build.restype = ctypes.c_int
+    L.gs_index_build_ex.argtypes = [P, P, P, I64, I64, I32, ctypes.c_int, ctypes.POINTER(gs_build_opts), P,
+                                    ctypes.POINTER(P)]
+    L.gs_index_build_ex.restype = ctypes.c_int
+    L.gs_index_info.argtypes = [P, ctypes.POINTER(gs_index_stats)]
+    L.gs_index_info.restype = ctypes.c_int
+    L.gs_index_get_layout.argtypes = [P, ctypes.POINTER(gs_index_layout)]
+    L.gs_index_get_layout.restype = ctypes.c_int
+    L.gs_index_free.argtypes = [P]
+    L.gs_index_free.restype = None
+    L.gs_search_workspace_size.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), I32,
+                                           ctypes.POINTER(SZ)]
+    L.gs_search_workspace_size.restype = ctypes.c_int
+    L.gs_search.argtypes = [P, P, P, P, I32, I64, I32, P, P, P, SZ, ctypes.POINTER(gs_search_opts), P]
+    L.gs_search.restype = ctypes.c_int
+    L.gs_search_host.argtypes = [P, P, P, P, I32, I64, I32, P, P, P, SZ, ctypes.POINTER(gs_search_opts), P]
+    L.gs_search_host.restype = ctypes.c_int
+    L.gs_score_dense.argtypes = [P, P, P, P, I32, I64, P, P, SZ, P]
+    L.gs_score_dense.restype = ctypes.c_int
+    L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
+    L.gs_search_flags.restype = ctypes.c_int
+    L.gs_status_str.argtypes = [ctypes.c_int]
+    L.gs_status_str.restype = ctypes.c_char_p
+    L.gs_last_cuda_error.argtypes = []
+    L.gs_last_cuda_error.restype = ctypes.c_char_p
+    L.gs_version.argtypes = []
+    L.gs_version.restype = I32
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != GS_OK:
+        raise GsError(status, what)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0) -> gs_search_opts:
+    o = gs_search_opts()
+    o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    o.group_queries, o.tile_docs = group_queries, tile_docs
+    o.chunk_blocks, o.sample_stride = chunk_blocks, sample_stride
+    return o
+
+
+@dataclass
+class Queries:
+    """A query batch as device CSR tensors (int32 indptr/terms, float32 weights)."""
+    indptr: torch.Tensor
+    terms: torch.Tensor
+    weights: torch.Tensor
+
+    @property
+    def batch(self) -> int:
+        return int(self.indptr.numel() - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.terms.numel())
+
+    @staticmethod
+    def from_numpy(indptr, terms, weights, device="cuda") -> "Queries":
+        return Queries(torch.as_tensor(indptr).to(device=device, dtype=torch.int32),
+                       torch.as_tensor(terms).to(device=device, dtype=torch.int32),
+                       torch.as_tensor(weights).to(device=device, dtype=torch.float32))
+
+
+class Index:
+    """Owner of a gs_index handle (device-resident inverted index)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        self._L = load()
+
+    @staticmethod
+    def build(doc_indptr: torch.Tensor, doc_terms: torch.Tensor, doc_w: torch.Tensor, vocab: int,
+              impact: str = "f32", tile_docs: int = 0, stream=None) -> "Index":
+        return gs_index_build(doc_indptr, doc_terms, doc_w, vocab, impact, tile_docs, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> gs_index_stats:
+        s = gs_index_stats()
+        _check(self._L.gs_index_info(self._h, ctypes.byref(s)), "gs_index_info")
+        return s
+
+    def layout(self) -> gs_index_layout:
+        lay = gs_index_layout()
+        _check(self._L.gs_index_get_layout(self._h, ctypes.byref(lay)), "gs_index_get_layout")
+        return lay
+
+    @property
+    def score_dtype(self):
+        return torch.int32 if self.stats().score_is_int else torch.float32
+
+    def workspace_size(self, batch: int, q_nnz: int, k: int, opts: gs_search_opts | None = None,
+                       host_io: bool = False) -> int:
+        n = ctypes.c_size_t(0)
+        _check(self._L.gs_search_workspace_size(self._h, batch, q_nnz, k, ctypes.byref(opts) if opts else None,
+                                                1 if host_io else 0, ctypes.byref(n)),
+               "gs_search_workspace_size")
+        return int(n.value)
+
+    def search(self, q: Queries, k: int, opts: gs_search_opts | None = None, workspace: torch.Tensor | None = None,
+               out_ids: torch.Tensor | None = None, out_scores: torch.Tensor | None = None, stream=None):
+        return gs_search(self, q, k, opts, workspace, out_ids, out_scores, stream)
+
+    def score_dense(self, q: Queries, workspace=None, stream=None) -> torch.Tensor:
+        return gs_score_dense(self, q, workspace, stream)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self._L.gs_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gs_index_build(doc_indptr, doc_terms, doc_w, vocab: int, impact: str = "f32", tile_docs: int = 0,
+                   stream=None) -> Index:
+    """Builds the index from device CSR tensors (int64 indptr, int32 terms, float32 weights)."""
+    L = load()
+    assert doc_indptr.dtype == torch.int64 and doc_terms.dtype == torch.int32 and doc_w.dtype == torch.float32
+    h = ctypes.c_void_p()
+    o = gs_build_opts()
+    o.tile_docs = tile_docs
+    _check(L.gs_index_build_ex(_ptr(doc_indptr), _ptr(doc_terms), _ptr(doc_w), doc_indptr.numel() - 1,
+                               doc_terms.numel(), vocab, IMPACTS[impact], ctypes.byref(o), _stream(stream),
+                               ctypes.byref(h)), "gs_index_build")
+    return Index(h)
+
+
+def alloc_workspace(index: Index, batch: int, q_nnz: int, k: int, opts=None, host_io=False, device=None):
+    n = index.workspace_size(batch, q_nnz, k, opts, host_io)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device or torch.device("cuda"))
+
+
+def gs_search(index: Index, q: Queries, k: int, opts=None, workspace=None, out_ids=None, out_scores=None,
+              stream=None):
+    """Exact top-k: returns (ids int32[B,k], scores float32|int32[B,k]) on the device (asynchronous)."""
+    L = load()
+    B = q.batch
+    dev = q.indptr.device
+    if workspace is None:
+        workspace = alloc_workspace(index, B, q.nnz, k, opts, device=dev)
+    if out_ids is None:
+        out_ids = torch.empty((B, k), dtype=torch.int32, device=dev)
+    if out_scores is None:
+        out_scores = torch.empty((B, k), dtype=index.score_dtype, device=dev)
+    _check(L.gs_search(index.handle, _ptr(q.indptr), _ptr(q.terms), _ptr(q.weights), B, q.nnz, k, _ptr(out_ids),
+                       _ptr(out_scores), _ptr(workspace), workspace.numel(), ctypes.byref(opts) if opts else None,
+                       _stream(stream)), "gs_search")
+    return out_ids, out_scores
+
+
+def gs_search_host(index: Index, h_indptr, h_terms, h_w, k: int, out_ids, out_scores, workspace, opts=None,
+                   stream=None):
+    """Host-memory queries and results (tensors on the CPU, ideally pinned); synchronous."""
+    L = load()
+    B = h_indptr.numel() - 1
+    _check(L.gs_search_host(index.handle, _ptr(h_indptr), _ptr(h_terms), _ptr(h_w), B, h_terms.numel(), k,
+                            _ptr(out_ids), _ptr(out_scores), _ptr(workspace), workspace.numel(),
+                            ctypes.byref(opts) if opts else None, _stream(stream)), "gs_search_host")
+    return out_ids, out_scores
+
+
+def gs_score_dense(index: Index, q: Queries, workspace=None, stream=None) -> torch.Tensor:
+    """Dense [B, N] score rows (Eq. 4) from the term-parallel scatter-add."""
+    L = load()
+    st = index.stats()
+    dev = q.indptr.device
+    o = make_opts("term_parallel")
+    if workspace is None:
+        workspace = alloc_workspace(index, q.batch, q.nnz, 1, o, device=dev)
+    rows = torch.empty((q.batch, st.num_docs), dtype=index.score_dtype, device=dev)
+    _check(L.gs_score_dense(index.handle, _ptr(q.indptr), _ptr(q.terms), _ptr(q.weights), q.batch, q.nnz,
+                            _ptr(rows), _ptr(workspace), workspace.numel(), _stream(stream)), "gs_score_dense")
+    return rows
+
+
+def gs_search_flags(workspace: torch.Tensor, stream=None) -> int:
+    """Synchronises the stream and returns the GS_FLAG_* bits of the last call on this workspace."""
+    L = load()
+    f = ctypes.c_uint32(0)
+    _check(L.gs_search_flags(_ptr(workspace), _stream(stream), ctypes.byref(f)), "gs_search_flags")
+    return int(f.value)
+
+
+def gs_version() -> int:
+    return int(load().gs_version())

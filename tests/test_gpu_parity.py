@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+uint8 impacts: ids and int32 scores bit-exact.  Float impacts: oracle/check.py
+criteria (i)-(iii) with tau = 1e-5 * A + 1e-6.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import check
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALGOS = ["term_parallel", "doc_tiled"]
+
+
+def _gs():
+    from paper_2606_26441_gb300 import gpusparse as gs
+    gs.load()
+    return gs
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _cudart():
+    """The CUDA runtime of the toolkit, for raw device-to-host copies of index arrays."""
+    import glob
+    import os
+    for cand in [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcudart.so")] + \
+            glob.glob("/usr/local/cuda*/lib64/libcudart.so*"):
+        if os.path.exists(cand):
+            lib = ctypes.CDLL(cand)
+            lib.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+            lib.cudaMemcpy.restype = ctypes.c_int
+            return lib
+    pytest.skip("libcudart.so not found")
+
+
+class Case:
+    """A collection + query batch + GPU index + oracle index for one impact type."""
+
+    def __init__(self, docs, qs, impact, tile_docs=0):
+        gs = _gs()
+        dev = _dev()
+        self.docs, self.qs, self.impact = docs, qs, impact
+        self.idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                                     torch.from_numpy(docs.weights).to(dev), docs.vocab, impact, tile_docs)
+        self.q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
+        self.ref = oracle.OracleIndex.from_batch(docs, impact)
+
+    def search(self, k, algo, **kw):
+        gs = _gs()
+        opts = gs.make_opts(algo, **kw)
+        ws = gs.alloc_workspace(self.idx, self.q.batch, self.q.nnz, k, opts)
+        ids, sc = gs.gs_search(self.idx, self.q, k, opts, ws)
+        flags = gs.gs_search_flags(ws)
+        return ids.cpu().numpy(), sc.cpu().numpy(), flags
+
+    def check(self, k, algo, **kw):
+        ids, sc, flags = self.search(k, algo, **kw)
+        assert flags == 0, f"flags {flags}"
+        rid, rsc, _ = self.ref.topk(self.qs.indptr, self.qs.terms, self.qs.weights, k)
+        if self.impact == "u8":
+            check.check_u8(ids, sc, rid, rsc)
+            return {}
+        return check.check_float(self.ref, self.qs.indptr, self.qs.terms, self.qs.weights, ids, sc, rid, rsc,
+                                 self.docs.n)
+
+
+@pytest.fixture(scope="module")
+def tiny_docs():
+    # 100K documents, 64 queries: the small workload; N is not a multiple of 32 or of a tile
+    return synth.docs(100_003, seed=0), synth.queries(64, seed=0)
+
+
+@pytest.fixture(scope="module")
+def cases(tiny_docs):
+    docs, qs = tiny_docs
+    return {imp: Case(docs, qs, imp) for imp in ("f32", "f16", "bf16", "u8")}
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("impact", ["f32", "f16", "bf16", "u8"])
+def test_topk_small_workload(cases, impact, algo):
+    stats = cases[impact].check(10, algo)
+    if stats:
+        assert stats["max_rel_err"] < 1e-5
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("impact", ["f32", "u8"])
+def test_topk_k1000_and_kmax(cases, impact, algo):
+    cases[impact].check(1000, algo)
+    cases[impact].check(2048, algo)
+    cases[impact].check(1, algo)
+
+
+@pytest.mark.parametrize("impact", ["f32", "u8"])
+def test_dense_rows_full_matrix(cases, impact):
+    """Every score of the [B, N] matrix (gs_score_dense) against the oracle rows."""
+    gs = _gs()
+    c = cases[impact]
+    rows = gs.gs_score_dense(c.idx, c.q).cpu().numpy()
+    ref_rows, _ = c.ref.rows(c.qs.indptr, c.qs.terms, c.qs.weights)
+    if impact == "u8":
+        check.check_rows(rows, ref_rows, "u8")
+    else:
+        absref = oracle.OracleIndex(c.docs.indptr, c.docs.terms, np.abs(c.docs.weights), c.docs.n, c.docs.vocab,
+                                    impact)
+        arows, _ = absref.rows(c.qs.indptr, c.qs.terms, np.abs(c.qs.weights))
+        check.check_rows(rows, ref_rows, impact, arows)
+
+
+def test_index_layout(cases):
+    """Sec. 3.2: doc-sorted lists, padded to 32 with (-1, 0), per-term metadata, segment table."""
+    gs = _gs()
+    for impact in ("f32", "u8", "bf16"):
+        c = cases[impact]
+        st = c.idx.stats()
+        lay = c.idx.layout()
+        V, bb = st.vocab, st.block_bytes
+        assert bb == {"f32": 256, "f16": 192, "bf16": 192, "u8": 160}[impact]
+
+        def d2h(ptr, nbytes):
+            out = np.empty(nbytes, dtype=np.uint8)
+            torch.cuda.synchronize()
+            rc = _cudart().cudaMemcpy(ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(ptr),
+                                      ctypes.c_size_t(nbytes), 2)  # cudaMemcpyDeviceToHost
+            assert rc == 0
+            return out
+        term_block = d2h(lay.term_block, 8 * (V + 1)).view(np.int64)
+        term_len = d2h(lay.term_len, 4 * V).view(np.int32)
+        max_score = d2h(lay.max_score, 4 * V).view(np.float32)
+        blocks = d2h(lay.blocks, st.blocks * bb).reshape(st.blocks, bb)
+        assert term_block[-1] == st.blocks
+        # Eq. 2: padded length = ceil(len / 32) * 32
+        assert np.array_equal(np.diff(term_block), (term_len.astype(np.int64) + 31) // 32)
+        assert st.postings == c.docs.nnz == int(term_len.sum())
+        assert st.posting_bytes == st.blocks * bb
+        ids = blocks[:, :128].copy().view(np.int32).reshape(-1)
+        imp_raw = blocks[:, 128:].copy()
+        if impact == "f32":
+            imp = imp_raw.view(np.float32).reshape(-1).astype(np.float64)
+        elif impact == "u8":
+            imp = imp_raw.reshape(-1).astype(np.float64)
+        else:
+            imp = torch.from_numpy(imp_raw.view(np.int16).reshape(-1)).view(torch.bfloat16).double().numpy()
+        rng = np.random.default_rng(0)
+        terms = np.concatenate([np.arange(20), rng.integers(0, V, 300)])
+        seg = None
+        if lay.seg:
+            seg = d2h(lay.seg, 4 * V * (st.num_tiles + 1)).view(np.uint32).reshape(V, st.num_tiles + 1)
+        for t in terms:
+            a, b = term_block[t] * 32, term_block[t + 1] * 32
+            L = term_len[t]
+            rdocs, rx = c.ref.posting_list(int(t))
+            assert L == len(rdocs)
+            assert np.array_equal(ids[a:a + L], rdocs)
+            assert np.array_equal(imp[a:a + L], rx)
+            assert np.all(ids[a + L:b] == -1) and np.all(imp[a + L:b] == 0)
+            if L:
+                assert max_score[t] == np.float32(rx.max())
+            if seg is not None:
+                bounds = np.arange(st.num_tiles + 1, dtype=np.int64) * st.tile_docs
+                assert np.array_equal(seg[t], np.searchsorted(rdocs, bounds, side="left"))
+
+
+def test_edge_cases():
+    """Empty and one-term queries, repeated terms, ragged sizes, B = 1."""
+    gs = _gs()
+    docs = synth.docs(5_000, seed=3)
+    base = synth.queries(6, seed=3)
+    rows = [([], []), ([base.terms[0]], [1.0]), ([7, 7, 9], [0.5, 0.25, 2.0])]
+    for i in range(3):
+        t, w = base.row(i)
+        rows.append((list(t), list(w)))
+    indptr = np.cumsum([0] + [len(r[0]) for r in rows]).astype(np.int64)
+    qs = synth.SparseBatch(indptr, np.array(sum([list(r[0]) for r in rows], []), np.int32),
+                           np.array(sum([list(r[1]) for r in rows], []), np.float32))
+    for impact in ("u8", "f32"):
+        c = Case(docs, qs, impact, tile_docs=256)
+        for algo in ALGOS:
+            for k in (1, 7, 300, 2048):
+                c.check(k, algo)
+    # a single query
+    single = qs.slice(3, 4)
+    c = Case(docs, single, "f32", tile_docs=256)
+    for algo in ALGOS:
+        c.check(5, algo)
+
+
+def test_bad_query_terms_are_flagged():
+    gs = _gs()
+    docs = synth.docs(3_000, seed=4)
+    qs = synth.queries(4, seed=4)
+    terms = qs.terms.copy()
+    terms[0] = 10 ** 6
+    w = qs.weights.copy()
+    w[3] = np.nan
+    bad = synth.SparseBatch(qs.indptr, terms, w)
+    c = Case(docs, bad, "f32", tile_docs=256)
+    ref_ids, ref_sc, flagged = c.ref.topk(bad.indptr, bad.terms, bad.weights, 5)
+    assert flagged
+    for algo in ALGOS:
+        ids, sc, flags = c.search(5, algo)
+        assert flags & gs.GS_FLAG_BAD_TERM
+        assert flags & gs.GS_FLAG_BAD_WEIGHT
+        check.check_float(c.ref, bad.indptr, bad.terms, bad.weights, ids, sc, ref_ids, ref_sc, docs.n)
+
+
+def test_argument_errors():
+    gs = _gs()
+    docs = synth.docs(1_000, seed=5)
+    qs = synth.queries(3, seed=5)
+    c = Case(docs, qs, "f32", tile_docs=256)
+    with pytest.raises(gs.GsError):
+        gs.gs_search(c.idx, c.q, docs.n + 1)
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_search(c.idx, c.q, 4096)
+    assert e.value.status == gs.GS_ERR_UNSUPPORTED
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_search(c.idx, c.q, 5, None, ws)
+    assert e.value.status == gs.GS_ERR_WORKSPACE
+    # invalid documents are rejected at build
+    bad_w = docs.weights.copy()
+    bad_w[0] = 7.0
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_index_build(torch.from_numpy(docs.indptr).cuda(), torch.from_numpy(docs.terms).cuda(),
+                          torch.from_numpy(bad_w).cuda(), docs.vocab, "u8")
+    assert e.value.status == gs.GS_ERR_DATA
+    dup = docs.terms.copy()
+    dup[1] = dup[0]
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_index_build(torch.from_numpy(docs.indptr).cuda(), torch.from_numpy(dup).cuda(),
+                          torch.from_numpy(docs.weights).cuda(), docs.vocab, "f32")
+    assert e.value.status == gs.GS_ERR_DATA
+
+
+def test_host_io_matches_device_path(cases):
+    gs = _gs()
+    c = cases["f32"]
+    k = 100
+    for algo in ALGOS:
+        opts = gs.make_opts(algo)
+        ids_d, sc_d = gs.gs_search(c.idx, c.q, k, opts)
+        ws = gs.alloc_workspace(c.idx, c.q.batch, c.q.nnz, k, opts, host_io=True)
+        h_ids = torch.empty((c.q.batch, k), dtype=torch.int32).pin_memory()
+        h_sc = torch.empty((c.q.batch, k), dtype=torch.float32).pin_memory()
+        gs.gs_search_host(c.idx, c.q.indptr.cpu().pin_memory(), c.q.terms.cpu().pin_memory(),
+                          c.q.weights.cpu().pin_memory(), k, h_ids, h_sc, ws, opts)
+        torch.cuda.synchronize()
+        rid, rsc, _ = c.ref.topk(c.qs.indptr, c.qs.terms, c.qs.weights, k)
+        check.check_float(c.ref, c.qs.indptr, c.qs.terms, c.qs.weights, h_ids.numpy(), h_sc.numpy(), rid, rsc,
+                          c.docs.n)
+
+
+def test_medium_workload_1m():
+    """1M documents, 128 queries, top-1000 on FP32 and uint8 impacts (uint8 bit-exact)."""
+    docs = synth.docs(1_000_000, seed=0)
+    qs = synth.queries(128, seed=0)
+    for impact in ("u8", "f32"):
+        c = Case(docs, qs, impact)
+        for algo in ALGOS:
+            c.check(1000, algo)
+        c.idx.free()
