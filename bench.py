@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Exact top-k sparse retrieval benchmark on GB300 (one JSON line on rank 0).
+
+Metric: exact top-1000 QPS and p50/p99 batch latency at 8.84M documents,
+batch 500 (the paper's scaling workload, Table 4), next to the plain FP32
+batched form (term-parallel scatter-add + dense top-k) on the same GPU, plus
+the HBM-roofline fraction of the dominant kernel.  A step = one gs_search of
+the whole batch: query prep, scoring, exact top-k.  Index build is outside the
+timed region (Sec. 3.2 builds it once).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank serves its own batch on its own GPU
+(replicas; no data-path collective); value = all ranks' queries / the slowest
+rank's time.  --impl reference times the CPU oracle (the reference arm of this
+benchmark) on the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "exact top-1000 QPS & p50/p99 ms @8.8M docs vs plain FP32 batch; % HBM peak"
+BYTES_PER_IMPACT = {"f32": 4, "f16": 2, "bf16": 2, "u8": 1}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="docs8.8m_b500_top1000", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--headline", default="f32:doc_tiled", help="impact:algo of the reported value")
+    ap.add_argument("--forms", default="f32:term_parallel,u8:doc_tiled,f16:doc_tiled,bf16:doc_tiled",
+                    help="other impact:algo forms measured beside the headline ('' = none)")
+    ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = one per core)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(statistics.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------- reference arm (CPU oracle)
+
+def run_reference(args, w, docs, qs):
+    import oracle
+    c = cores()
+    per_step = args.cpu_queries or c
+    t0 = time.perf_counter()
+    ref = oracle.OracleIndex.from_batch(docs, "f32")
+    build_s = time.perf_counter() - t0
+    times = []
+    n_q = qs.n
+    for step in range(args.warmup + args.steps):
+        lo = (step * per_step) % max(1, n_q - per_step + 1)
+        sub = qs.slice(lo, lo + per_step)
+        t = time.perf_counter()
+        ref.topk(sub.indptr, sub.terms, sub.weights, w.k, threads=c)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    qps = per_step * len(times) / total
+    ms = [t * 1e3 for t in times]
+    return {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "QPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, "f32", "oracle (CPU, FP64 term walk + full sort)"),
+        "cpu_baseline": {"value": qps, "unit": "QPS", "cores": c, "kind": "oracle",
+                         "sample": f"{per_step} queries per step of the {w.batch}-query batch, full "
+                                   f"{w.n_docs}-doc collection; oracle index build {build_s:.1f}s untimed"},
+        "e2e": {"value": qps, "unit": "QPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def workload_config(w, impact, algo):
+    return {"workload": w.name, "n_docs": w.n_docs, "batch": w.batch, "k": w.k, "impact": impact, "algo": algo,
+            "vocab": synth.VOCAB, "doc_nnz": "Poisson(120) in [1,400]", "query_nnz": "Poisson(24) in [1,64]",
+            "terms": "Zipf(1.1) over a seeded vocabulary permutation", "weights": "lognormal(-0.5,0.8) clipped (0,5]",
+            "l2": "no flush: the posting index (GBs) is far larger than the 129 MB L2",
+            "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
+    """Algorithmic bytes of the dominant kernel per launch.
+
+    doc_tiled main pass : sum over groups of sum over the group's distinct terms
+                          of the term's postings outside the sample tiles,
+                          times (4 + impact bytes);
+    term_parallel scatter: sum over (query, term) of the term's postings times
+                          (4 + impact bytes), plus 4 B per score-row element
+                          (each row is updated in place once it is zeroed).
+    """
+    b = 4 + BYTES_PER_IMPACT[impact]
+    df = layout_info["df"]
+    if algo == "term_parallel":
+        post = int(df[qs.terms].sum())
+        return post * b + 4 * qs.n * docs.n, {"postings": post}
+    G = plan.group_queries
+    main_df = df - layout_info["sample_df"]
+    post = 0
+    for g0 in range(0, qs.n, G):
+        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
+        u = np.unique(qs.terms[a:e])
+        post += int(main_df[u].sum())
+    return post * b, {"postings": post}
+
+
+def sample_term_counts(docs, T, R, n_sample):
+    """Postings of every term inside the sample tiles (tiles j * R, j < n_sample)."""
+    cnt = np.zeros(docs.vocab, dtype=np.int64)
+    if R <= 0 or n_sample <= 0:
+        return cnt
+    for j in range(n_sample):
+        d0 = j * R * T
+        a, e = int(docs.indptr[d0]), int(docs.indptr[min(docs.n, d0 + T)])
+        cnt += np.bincount(docs.terms[a:e], minlength=docs.vocab)
+    return cnt
+
+
+def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sample_clocks=False):
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_NUM_STAGE_EVENTS)] for _ in range(steps)]
+    opts_plain = gs.make_opts(algo)
+    opts_t = [gs.make_opts(algo, stage_events=e) for e in ev]
+    ws = gs.alloc_workspace(idx, q.batch, q.nnz, k, opts_plain)
+    out_ids = torch.empty((q.batch, k), dtype=torch.int32, device=q.indptr.device)
+    out_sc = torch.empty((q.batch, k), dtype=idx.score_dtype, device=q.indptr.device)
+    for _ in range(warmup):
+        gs.gs_search(idx, q, k, opts_plain, ws, out_ids, out_sc)
+    flags = gs.gs_search_flags(ws)
+    if flags:
+        raise RuntimeError(f"search raised flags {flags}")
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = None
+    launches0 = gs.gs_kernel_launches()
+    sampler = ClockSampler(device_index) if sample_clocks else None
+    if sampler:
+        sampler.__enter__()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        gs.gs_search(idx, q, k, opts_t[i], ws, out_ids, out_sc)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if sampler:
+        sampler.__exit__()
+        clocks = sampler.summary()
+    launches = gs.gs_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per_step = [e[0].elapsed_time(e[-1]) for e in ev]
+    span = ev[0][0].elapsed_time(ev[-1][-1])
+    stages = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(len(e) - 1)] for e in ev])
+    return {"span_ms": span, "per_step_ms": per_step, "stage_ms": stages.mean(axis=0).tolist(), "wall_s": wall,
+            "launches": launches, "clocks": clocks, "ids": out_ids, "scores": out_sc, "ws": ws}
+
+
+def e2e_form(gs, torch, idx, qs, k, algo, steps, warmup):
+    """Same metric through gs_search_host: pinned host queries in, host results out, copies timed."""
+    opts = gs.make_opts(algo)
+    B = qs.n
+    h_indptr = torch.from_numpy(qs.indptr.astype(np.int32)).pin_memory()
+    h_terms = torch.from_numpy(qs.terms).pin_memory()
+    h_w = torch.from_numpy(qs.weights).pin_memory()
+    h_ids = torch.empty((B, k), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((B, k), dtype=idx.score_dtype).pin_memory()
+    ws = gs.alloc_workspace(idx, B, qs.nnz, k, opts, host_io=True)
+    for _ in range(warmup):
+        gs.gs_search_host(idx, h_indptr, h_terms, h_w, k, h_ids, h_sc, ws, opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gs.gs_search_host(idx, h_indptr, h_terms, h_w, k, h_ids, h_sc, ws, opts)
+    dt = time.perf_counter() - t0
+    h2d = h_indptr.numel() * 4 + h_terms.numel() * 4 + h_w.numel() * 4
+    d2h = B * k * 8
+    return {"value": B * steps / dt, "unit": "QPS", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": dt / steps * 1e3, "api": "gs_search_host"}
+
+
+def run_gpu(args, w, docs, qs, world, rank, local):
+    import torch
+    from paper_2606_26441_gb300 import gpusparse as gs
+    gs.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    k = w.k
+    d_indptr = torch.from_numpy(docs.indptr).to(dev)
+    d_terms = torch.from_numpy(docs.terms).to(dev)
+    d_w = torch.from_numpy(docs.weights).to(dev)
+    q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
+    df = np.bincount(docs.terms, minlength=docs.vocab).astype(np.int64)
+
+    head_imp, head_algo = args.headline.split(":")
+    forms = [(head_imp, head_algo)] + [tuple(f.split(":")) for f in args.forms.split(",") if f]
+    indexes = {}
+    results = {}
+    for imp, algo in forms:
+        if imp not in indexes:
+            indexes[imp] = gs.gs_index_build(d_indptr, d_terms, d_w, docs.vocab, imp)
+        idx = indexes[imp]
+        r = time_form(gs, torch, idx, q, k, algo, args.steps, args.warmup, dist, local,
+                      sample_clocks=(imp, algo) == (head_imp, head_algo))
+        plan = idx.plan(q.batch, q.nnz, k, gs.make_opts(algo))
+        results[(imp, algo)] = (r, plan, idx)
+
+    # headline
+    r, plan, idx = results[(head_imp, head_algo)]
+    span_s = r["span_ms"] / 1e3
+    if dist:
+        t = torch.tensor([span_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        span_s = float(t.item())
+    value = w.batch * args.steps * world / span_s
+    st = idx.stats()
+    # dominant kernel: the scoring stage (stage 3 -> 4)
+    stage_names = ["query_prep", "sample_scoring" if head_algo == "doc_tiled" else "zero_rows",
+                   "sample_topk", "scoring", "final_topk"]
+    T, R, ns = plan.tile_docs, plan.sample_stride, plan.sample_tiles
+    layout_info = {"df": df, "sample_df": sample_term_counts(docs, T, R, ns) if head_algo == "doc_tiled" else 0}
+    alg_bytes, extra = algorithmic_bytes(plan, docs, qs, head_imp, head_algo, layout_info)
+    kern_ms = r["stage_ms"][3]
+    peak, peak_src = load_peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    # (query, posting) updates the scoring kernel performs
+    upd_df = df - layout_info["sample_df"] if head_algo == "doc_tiled" else df
+    updates = int(upd_df[qs.terms].sum())
+    forms_out = {}
+    for (imp, algo), (rr, pl, ix) in results.items():
+        ms = rr["per_step_ms"]
+        forms_out[f"{imp}:{algo}"] = {
+            "qps": w.batch * len(ms) / (rr["span_ms"] / 1e3), "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "per_query_ms": float(np.mean(ms)) / w.batch,
+            "stage_ms": dict(zip(stage_names if algo == "doc_tiled" else
+                                 ["query_prep", "zero_rows", "-", "scoring", "topk"], rr["stage_ms"])),
+            "index_bytes": int(ix.stats().posting_bytes), "meta_bytes": int(ix.stats().meta_bytes)}
+    plain = forms_out.get("f32:term_parallel")
+    out = {
+        "metric": METRIC, "value": value, "unit": "QPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(r["per_step_ms"])), "p50_ms": float(np.percentile(r["per_step_ms"], 50)),
+        "p99_ms": float(np.percentile(r["per_step_ms"], 99)), "per_query_ms": float(np.mean(r["per_step_ms"])) / w.batch,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head_imp, "data": "synthetic",
+        "config": workload_config(w, head_imp, head_algo),
+        "plan": {"group_queries": plan.group_queries, "tile_docs": plan.tile_docs, "sample_stride": plan.sample_stride,
+                 "sample_tiles": plan.sample_tiles, "cand_capacity": int(plan.cand_capacity)},
+        "vs_plain_fp32": (value / plain["qps"]) if plain and (head_imp, head_algo) != ("f32", "term_parallel") else None,
+        "forms": forms_out,
+        "roofline": {"bound": "hbm", "kernel": "dt_tile_kernel (main pass)" if head_algo == "doc_tiled"
+                     else "tp_scatter_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                     "traffic": None, "algorithmic_bytes": alg_bytes, "kernel_ms": kern_ms,
+                     "postings_read": extra["postings"], "scatter_updates": updates,
+                     "updates_per_s": updates / (kern_ms / 1e3)},
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+    }
+    if not args.no_e2e:
+        out["e2e"] = e2e_form(gs, torch, idx, qs, k, head_algo, max(3, args.steps // 2), 2)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    w = synth.WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    docs = synth.docs(w.n_docs, seed=0, threads=cores())
+    qs = synth.queries(w.batch, seed=rank, law=w.query_law)
+    gen_s = time.perf_counter() - t0
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        out = run_reference(args, w, docs, qs)
+        print(json.dumps(out), flush=True)
+        return
+    out = run_gpu(args, w, docs, qs, world, rank, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        c = cores()
+        nq = args.cpu_queries or c
+        ref = oracle.OracleIndex.from_batch(docs, args.headline.split(":")[0])
+        sub = qs.slice(0, nq)
+        t = time.perf_counter()
+        ref.topk(sub.indptr, sub.terms, sub.weights, w.k, threads=c)
+        dt = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": nq / dt, "unit": "QPS", "cores": c, "kind": "oracle",
+                               "sample": f"first {nq} of the {w.batch} queries over the full {w.n_docs}-doc "
+                                         f"collection ({dt:.1f}s wall on {c} threads)"}
+    out["setup_s"] = {"generate": gen_s}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,13 @@ typedef struct {
   const uint32_t* seg;        /* see above; NULL without a tile table */
 } gs_index_layout;
 
+/* Stage boundaries at which gs_search records the caller's CUDA events when
+ * gs_search_opts.stage_events is set (timing only; no work is skipped):
+ *   [0] start  [1] after query prep  [2] after sample scoring (DOC_TILED) or
+ *   score-row zeroing (TERM_PARALLEL)  [3] after the sample top-k
+ *   [4] after the main scoring kernel  [5] end, after the final top-k. */
+#define GS_NUM_STAGE_EVENTS 6
+
 typedef struct {
   int32_t algo;          /* gs_algo */
   int32_t group_queries; /* DOC_TILED: queries per group (0 = auto) */
@@ -147,7 +154,8 @@ typedef struct {
   int32_t sample_stride; /* DOC_TILED: 1 of every R tiles forms the threshold
                             sample (0 = auto, 1 = no sampling: every
                             document is a candidate) */
-  int32_t reserved[3];
+  int32_t reserved;
+  void* const* stage_events; /* NULL, or GS_NUM_STAGE_EVENTS cudaEvent_t */
 } gs_search_opts;
 
 /* --- index --------------------------------------------------------------- */
@@ -217,6 +225,24 @@ gs_status gs_score_dense(const gs_index* index, const int32_t* q_indptr, const i
                          const float* q_w, int32_t batch, int64_t q_nnz, void* out_rows,
                          void* workspace, size_t workspace_bytes, gs_stream_t stream);
 
+/* The plan gs_search resolves for these arguments (kernel, tile shapes,
+ * sample stride), for inspection and performance accounting. */
+typedef struct {
+  int32_t algo;          /* resolved gs_algo */
+  int32_t group_queries; /* DOC_TILED: G */
+  int32_t tile_docs;     /* DOC_TILED: T */
+  int32_t sample_stride; /* DOC_TILED: R (0: no sample, every doc a candidate) */
+  int32_t num_groups;
+  int32_t num_tiles;
+  int32_t sample_tiles;  /* tiles j * R, j < sample_tiles, form the sample */
+  int32_t chunk_blocks;  /* TERM_PARALLEL: blocks per work item */
+  int64_t cand_capacity; /* DOC_TILED: candidate slots per query */
+  int64_t reserved[4];
+} gs_plan_info;
+
+gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
+                         const gs_search_opts* opts, gs_plan_info* out);
+
 /* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits the last
  * call that used `workspace` raised. */
 gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags);
@@ -227,6 +253,8 @@ const char* gs_status_str(gs_status status);
 /* the CUDA error string of the last GS_ERR_CUDA on this host thread */
 const char* gs_last_cuda_error(void);
 int32_t gs_version(void); /* major * 10000 + minor * 100 + patch */
+/* number of CUDA kernels this library has launched in the process so far */
+int64_t gs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,7 @@
 // Small C-ABI helpers: status strings, CUDA error capture, version.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 
@@ -11,6 +12,14 @@ namespace gs {
 static thread_local cudaError_t t_last_cuda = cudaSuccess;
 
 void set_cuda_error(cudaError_t e) { t_last_cuda = e; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void record_stage(const gs_search_opts* opts, int i, cudaStream_t s) {
+  if (opts && opts->stage_events && i >= 0 && i < GS_NUM_STAGE_EVENTS && opts->stage_events[i])
+    cudaEventRecord(static_cast<cudaEvent_t>(opts->stage_events[i]), s);
+}
 
 int device_sm_count(int device) {
   static std::mutex mu;
@@ -43,3 +52,5 @@ extern "C" const char* gs_status_str(gs_status s) {
 extern "C" const char* gs_last_cuda_error(void) { return cudaGetErrorString(gs::t_last_cuda); }
 
 extern "C" int32_t gs_version(void) { return 100; }
+
+extern "C" int64_t gs_kernel_launches(void) { return gs::g_launches.load(); }

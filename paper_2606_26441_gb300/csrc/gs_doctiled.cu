@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
 
 template <int IMPACT>
 gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
-                       const DtPlan& p, cudaStream_t s) {
+                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
   const size_t smem = (size_t)c.G * c.T * 4;
   auto ks = dt_tile_kernel<IMPACT, kModeSample>;
   auto km = dt_tile_kernel<IMPACT, kModeMain>;
@@ -519,6 +519,7 @@ gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32
                                                    p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.samp_sc, k,
                                                    p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words);
     GS_LAUNCH_CHECK();
+    record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
       topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.samp),
                                                                 c.sample_docs, c.sample_docs, k, p.samp_ids,
@@ -528,16 +529,35 @@ gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32
                                                               c.sample_docs, c.sample_docs, k, p.samp_ids,
                                                               reinterpret_cast<float*>(p.samp_sc));
     GS_LAUNCH_CHECK();
+  } else {
+    record_stage(opts, 2, s);
   }
+  record_stage(opts, 3, s);
   km<<<c.nt * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B,
                                            q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent,
                                            p.samp, c.sample_docs, p.samp_sc, k, p.cand, p.cand_cnt, c.cap,
                                            p.tiebm, c.bm_words);
   GS_LAUNCH_CHECK();
+  record_stage(opts, 4, s);
   return GS_OK;
 }
 
 }  // namespace
+
+gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search_opts* opts, gs_plan_info* out) {
+  DtConfig c;
+  gs_status st = dt_config(ix, B, k, opts, &c);
+  if (st != GS_OK) return st;
+  out->algo = GS_ALGO_DOC_TILED;
+  out->group_queries = c.G;
+  out->tile_docs = c.T;
+  out->sample_stride = c.R;
+  out->num_groups = c.ng;
+  out->num_tiles = c.nt;
+  out->sample_tiles = c.n_sample;
+  out->cand_capacity = c.cap;
+  return GS_OK;
+}
 
 gs_status dt_workspace_bytes(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k, const gs_search_opts* opts,
                              size_t* bytes) {
@@ -557,15 +577,17 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   size_t need = 0;
   DtPlan p = carve_dt(ws, ix, B, q_nnz, k, c, &need);
   if (need > ws_bytes) return GS_ERR_WORKSPACE;
+  record_stage(opts, 0, s);
   dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt, p.u_terms, p.u_ptr,
                                        p.n_u, p.ent, flags);
   GS_LAUNCH_CHECK();
   GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
+  record_stage(opts, 1, s);
   switch (ix->impact) {
-    case GS_IMPACT_F32: st = launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
-    case GS_IMPACT_F16: st = launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
-    case GS_IMPACT_BF16: st = launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
-    default: st = launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, s); break;
+    case GS_IMPACT_F32: st = launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
+    case GS_IMPACT_F16: st = launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
+    case GS_IMPACT_BF16: st = launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
+    default: st = launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
   }
   if (st != GS_OK) return st;
   if (c.R > 0) {
@@ -585,6 +607,7 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
     dt_final_kernel<float><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.samp_sc,
                                               c.R, k, out_ids, static_cast<float*>(out_scores), flags);
   GS_LAUNCH_CHECK();
+  record_stage(opts, 5, s);
   return GS_OK;
 }
 

@@ -9,6 +9,9 @@ namespace gs {
 gs_status dt_workspace_bytes(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k, const gs_search_opts* opts,
                              size_t* bytes);
 
+// Resolved doc-tiled plan (G, T, R, ...) for gs_search_plan.
+gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search_opts* opts, gs_plan_info* out);
+
 // Runs the doc-tiled search on `s`; flags: the workspace flag word.
 gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* q_terms, const float* q_w,
                     int32_t B, int64_t q_nnz, int32_t k, int32_t* out_ids, void* out_scores, void* ws,

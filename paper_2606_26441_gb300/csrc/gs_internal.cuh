@@ -100,6 +100,9 @@ struct Carver {
 // error helpers
 void set_cuda_error(cudaError_t e);
 int device_sm_count(int device);
+// launch accounting and stage events
+void count_launches(int n);
+void record_stage(const gs_search_opts* opts, int i, cudaStream_t s);
 
 }  // namespace gs
 
@@ -112,11 +115,14 @@ int device_sm_count(int device);
     }                                     \
   } while (0)
 
-#define GS_LAUNCH_CHECK()                   \
+// checks the launch(es) just made and counts n kernels
+#define GS_LAUNCH_CHECK_N(n)                \
   do {                                      \
     cudaError_t _e = cudaGetLastError();    \
     if (_e != cudaSuccess) {                \
       gs::set_cuda_error(_e);               \
       return GS_ERR_CUDA;                   \
     }                                       \
+    gs::count_launches(n);                  \
   } while (0)
+#define GS_LAUNCH_CHECK() GS_LAUNCH_CHECK_N(1)

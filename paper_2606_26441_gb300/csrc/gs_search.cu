@@ -267,11 +267,17 @@ void launch_tp_scatter(const gs_index* ix, const TpPlan& p, int64_t q_nnz, int c
 
 gs_status run_tp_scores(const gs_index* ix, const int32_t* q_indptr, const int32_t* q_terms, const float* q_w,
                         int32_t B, int64_t q_nnz, const TpPlan& p, int chunk, void* rows, int64_t ld,
-                        cudaStream_t s) {
+                        const gs_search_opts* opts, cudaStream_t s) {
+  record_stage(opts, 0, s);
   tp_prep_kernel<<<1, kPrepThreads, 0, s>>>(q_indptr, q_terms, q_w, B, q_nnz, ix->V, ix->impact, ix->term_block,
                                             chunk, p.pair_q, p.pair_t, p.pair_wf, p.pair_wi, p.pair_chunk, p.hdr);
+  GS_LAUNCH_CHECK();
+  record_stage(opts, 1, s);
   const int64_t words = (int64_t)B * ld;
   zero_kernel<<<persistent_grid(ix, 4), 512, 0, s>>>(static_cast<uint32_t*>(rows), words);
+  GS_LAUNCH_CHECK();
+  record_stage(opts, 2, s);
+  record_stage(opts, 3, s);
   switch (ix->impact) {
     case GS_IMPACT_F32: launch_tp_scatter<GS_IMPACT_F32>(ix, p, q_nnz, chunk, rows, ld, s); break;
     case GS_IMPACT_F16: launch_tp_scatter<GS_IMPACT_F16>(ix, p, q_nnz, chunk, rows, ld, s); break;
@@ -279,6 +285,7 @@ gs_status run_tp_scores(const gs_index* ix, const int32_t* q_indptr, const int32
     default: launch_tp_scatter<GS_IMPACT_U8>(ix, p, q_nnz, chunk, rows, ld, s); break;
   }
   GS_LAUNCH_CHECK();
+  record_stage(opts, 4, s);
   return GS_OK;
 }
 
@@ -362,9 +369,11 @@ extern "C" gs_status gs_search(const gs_index* ix, const int32_t* q_indptr, cons
   }
   if (algo == GS_ALGO_DOC_PARALLEL) return GS_ERR_UNSUPPORTED;
   const int chunk = (opts && opts->chunk_blocks > 0) ? opts->chunk_blocks : kDefaultChunkBlocks;
-  st = run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, chunk, p.rows, p.ld, s);
+  st = run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, chunk, p.rows, p.ld, opts, s);
   if (st != GS_OK) return st;
-  return run_topk_dense(ix, p.rows, p.ld, B, k, out_ids, out_scores, s);
+  st = run_topk_dense(ix, p.rows, p.ld, B, k, out_ids, out_scores, s);
+  record_stage(opts, 5, s);
+  return st;
 }
 
 extern "C" gs_status gs_score_dense(const gs_index* ix, const int32_t* q_indptr, const int32_t* q_terms,
@@ -384,7 +393,7 @@ extern "C" gs_status gs_score_dense(const gs_index* ix, const int32_t* q_indptr,
   size_t tp_bytes = 0;
   TpPlan p = carve_tp(workspace, ix, B, q_nnz, false, &tp_bytes);
   GS_CUDA_TRY(cudaMemsetAsync(p.hdr, 0, sizeof(Header), s));
-  return run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, kDefaultChunkBlocks, out_rows, ix->N, s);
+  return run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, kDefaultChunkBlocks, out_rows, ix->N, nullptr, s);
 }
 
 extern "C" gs_status gs_search_host(const gs_index* ix, const int32_t* h_q_indptr, const int32_t* h_q_terms,
@@ -417,6 +426,19 @@ extern "C" gs_status gs_search_host(const gs_index* ix, const int32_t* h_q_indpt
   GS_CUDA_TRY(cudaMemcpyAsync(h_out_ids, io.ids, sizeof(int32_t) * B * (size_t)k, cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaMemcpyAsync(h_out_scores, io.scores, sizeof(uint32_t) * B * (size_t)k, cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaStreamSynchronize(s));
+  return GS_OK;
+}
+
+extern "C" gs_status gs_search_plan(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k,
+                                    const gs_search_opts* opts, gs_plan_info* out) {
+  if (!out) return GS_ERR_INVALID_ARG;
+  gs_status st = check_query_args(ix, B, q_nnz, k, true);
+  if (st != GS_OK) return st;
+  std::memset(out, 0, sizeof(*out));
+  const int algo = resolve_algo(ix, opts);
+  if (algo == GS_ALGO_DOC_TILED) return dt_plan_info(ix, B, k, opts, out);
+  out->algo = algo;
+  out->chunk_blocks = (opts && opts->chunk_blocks > 0) ? opts->chunk_blocks : kDefaultChunkBlocks;
   return GS_OK;
 }
 

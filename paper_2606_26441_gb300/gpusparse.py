@@ -27,8 +27,10 @@ GS_MAX_K = 2048
 EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
-    "gs_status_str", "gs_last_cuda_error", "gs_version",
+    "gs_search_plan",
+    "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
 )
+GS_NUM_STAGE_EVENTS = 6
 
 
 class GsError(RuntimeError):
@@ -60,7 +62,14 @@ class gs_index_layout(ctypes.Structure):
 class gs_search_opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
                 ("chunk_blocks", ctypes.c_int32), ("sample_stride", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("reserved", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p))]
+
+
+class gs_plan_info(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
+                ("sample_stride", ctypes.c_int32), ("num_groups", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
+                ("sample_tiles", ctypes.c_int32), ("chunk_blocks", ctypes.c_int32),
+                ("cand_capacity", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
 
 
 _lib = None
@@ -96,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.gs_search_host.restype = ctypes.c_int
     L.gs_score_dense.argtypes = [P, P, P, P, I32, I64, P, P, SZ, P]
     L.gs_score_dense.restype = ctypes.c_int
+    L.gs_search_plan.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), ctypes.POINTER(gs_plan_info)]
+    L.gs_search_plan.restype = ctypes.c_int
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -104,6 +115,8 @@ def load(path: str = LIB_PATH):
     L.gs_last_cuda_error.restype = ctypes.c_char_p
     L.gs_version.argtypes = []
     L.gs_version.restype = I32
+    L.gs_kernel_launches.argtypes = []
+    L.gs_kernel_launches.restype = I64
     _lib = L
     return L
 
@@ -123,11 +136,18 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0) -> gs_search_opts:
+def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0,
+              stage_events=None) -> gs_search_opts:
+    """stage_events: None or GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
     o = gs_search_opts()
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.group_queries, o.tile_docs = group_queries, tile_docs
     o.chunk_blocks, o.sample_stride = chunk_blocks, sample_stride
+    if stage_events is not None:
+        assert len(stage_events) == GS_NUM_STAGE_EVENTS
+        arr = (ctypes.c_void_p * GS_NUM_STAGE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in stage_events])
+        o._events_keepalive = arr
+        o.stage_events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
     return o
 
 
@@ -190,6 +210,12 @@ class Index:
                                                 1 if host_io else 0, ctypes.byref(n)),
                "gs_search_workspace_size")
         return int(n.value)
+
+    def plan(self, batch: int, q_nnz: int, k: int, opts: gs_search_opts | None = None) -> gs_plan_info:
+        out = gs_plan_info()
+        _check(self._L.gs_search_plan(self._h, batch, q_nnz, k, ctypes.byref(opts) if opts else None,
+                                      ctypes.byref(out)), "gs_search_plan")
+        return out
 
     def search(self, q: Queries, k: int, opts: gs_search_opts | None = None, workspace: torch.Tensor | None = None,
                out_ids: torch.Tensor | None = None, out_scores: torch.Tensor | None = None, stream=None):
@@ -282,3 +308,7 @@ def gs_search_flags(workspace: torch.Tensor, stream=None) -> int:
 
 def gs_version() -> int:
     return int(load().gs_version())
+
+
+def gs_kernel_launches() -> int:
+    return int(load().gs_kernel_launches())

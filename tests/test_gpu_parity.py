@@ -218,7 +218,7 @@ def test_bad_query_terms_are_flagged():
 
 def test_argument_errors():
     gs = _gs()
-    docs = synth.docs(1_000, seed=5)
+    docs = synth.docs(5_000, seed=5)
     qs = synth.queries(3, seed=5)
     c = Case(docs, qs, "f32", tile_docs=256)
     with pytest.raises(gs.GsError):
