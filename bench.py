@@ -218,6 +218,10 @@ def sample_term_counts(docs, T, R, n_sample):
 
 def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sample_clocks=False):
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_NUM_STAGE_EVENTS)] for _ in range(steps)]
+    for e in ev:  # torch creates the CUDA event on its first record; the library re-records it
+        for x in e:
+            x.record()
+    torch.cuda.synchronize()
     opts_plain = gs.make_opts(algo)
     opts_t = [gs.make_opts(algo, stage_events=e) for e in ev]
     ws = gs.alloc_workspace(idx, q.batch, q.nnz, k, opts_plain)

@@ -33,7 +33,9 @@ namespace gs {
 namespace {
 
 constexpr int kDtThreads = 1024;
-constexpr int kDtMaxAccBytes = 192 * 1024;
+constexpr int kDtMaxAccBytes = 128 * 1024;  // G x T accumulators
+constexpr int kEntCap = 4096;                // query entries staged in shared memory (32 KB)
+constexpr int kItemCap = 9216;               // (term, 128-posting chunk) items per term batch (18 KB)
 constexpr int kDefaultGroup = 32;
 constexpr int kDefaultSampleStride = 16;
 
@@ -214,13 +216,17 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
+  // dynamic shared memory: [G x T accumulators][staged query entries][item -> term]
   extern __shared__ __align__(16) uint8_t dyn_smem[];
   AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
+  uint2* ent_s = reinterpret_cast<uint2*>(dyn_smem + (size_t)G * T * sizeof(AccT));
+  uint16_t* item_term = reinterpret_cast<uint16_t*>(ent_s + kEntCap);
   __shared__ uint32_t s_start[kDtThreads], s_end[kDtThreads];
   __shared__ int32_t s_item[kDtThreads + 1];
   __shared__ int64_t s_blk0[kDtThreads];
   __shared__ int32_t s_e0[kDtThreads], s_e1[kDtThreads];
   __shared__ int warp_buf[32];
+  __shared__ int s_next;
 
   const int g = blockIdx.x % ng;
   const int tile_idx = blockIdx.x / ng;
@@ -236,19 +242,31 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   const int64_t doc0 = (int64_t)tau * T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  for (int i = threadIdx.x; i < G * T; i += blockDim.x) acc[i] = (AccT)0;
-
+  {
+    uint4* a4 = reinterpret_cast<uint4*>(acc);
+    for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
+  }
   const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
   const int nterm = n_u[g];
   const int32_t* ut = u_terms + ebase;
   const int32_t* up = u_ptr + ebase + g;
   const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
+  // the group's (query, weight) entries, staged in shared memory when they fit
+  const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
+  const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
+  const bool staged = (ent_hi - ent_lo) <= kEntCap;
+  if (staged)
+    for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) ent_s[i] = __ldg(ent + ent_lo + i);
+  const uint2* E_ptr = staged ? ent_s : ent + ent_lo;  // indexed by entry position - ent_lo
+  // terms per batch: their 128-posting work items must fit the item table
+  const int items_per_term = T / 128 + 1;
+  const int tb = min(kDtThreads, kItemCap / items_per_term);
   __syncthreads();
 
-  for (int j0 = 0; j0 < nterm; j0 += kDtThreads) {
+  for (int j0 = 0; j0 < nterm; j0 += tb) {
     const int j = j0 + threadIdx.x;
     int items = 0;
-    if (j < nterm) {
+    if (threadIdx.x < tb && j < nterm) {
       const int32_t t = ut[j];
       const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
       const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
@@ -257,35 +275,62 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       s_blk0[threadIdx.x] = __ldg(term_block + t) + (s >> 5);
       s_e0[threadIdx.x] = __ldg(up + j);
       s_e1[threadIdx.x] = __ldg(up + j + 1);
-      if (e > s) items = (int)(((e - 1) >> 5) - (s >> 5) + 1);
+      if (e > s) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
     }
     int total;
     const int xi = block_excl_scan(items, warp_buf, &total);
-    s_item[threadIdx.x] = xi;
-    if (threadIdx.x == 0) s_item[kDtThreads] = total;
-    const int nloc = min(kDtThreads, nterm - j0);
+    if (threadIdx.x < tb) s_item[threadIdx.x] = xi;
+    for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
+    if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    for (int it = warp; it < total; it += kDtThreads / 32) {
-      const int jj = ub_i32(s_item, nloc, it) - 1;
-      const int b = it - s_item[jj];
+    // dynamic work distribution over (term, 4-block chunk) items
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&s_next, 1);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    while (nxt < total) {
+      const int it = nxt;
+      if (lane == 0) nxt = atomicAdd(&s_next, 1);
+      nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      const int jj = item_term[it];
+      const int c = it - s_item[jj];
       const uint32_t s = s_start[jj], e = s_end[jj];
-      const uint32_t pos = ((s >> 5) + (uint32_t)b) * 32u + (uint32_t)lane;
-      const bool valid = pos >= s && pos < e;
-      const uint8_t* blk = blocks + (s_blk0[jj] + b) * bb;
-      const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
-      const int dl = (int)(doc - doc0);
-      const int32_t eb = s_e0[jj], ee = s_e1[jj];
-      if (IMPACT == GS_IMPACT_U8) {
-        const int x = (int)__ldg(blk + 128 + lane);
-        for (int32_t en = eb; en < ee; ++en) {
-          const uint2 E = __ldg(ent + en);
-          if (valid) atomicAdd(reinterpret_cast<int32_t*>(acc) + E.x * T + dl, (int32_t)E.y * x);
+      const uint32_t fb = (s >> 5) + 4u * (uint32_t)c;  // first block of the chunk (list-relative)
+      const uint32_t lb = (e - 1) >> 5;                // last block of the segment
+      const uint8_t* base = blocks + (s_blk0[jj] + 4 * c) * bb;
+      int dl[4];
+      AccT x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        dl[i] = -1;
+        x[i] = (AccT)0;
+        const uint32_t b = fb + (uint32_t)i;
+        if (b <= lb) {
+          const uint8_t* blk = base + i * bb;
+          const uint32_t pos = b * 32u + (uint32_t)lane;
+          const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
+          if (pos >= s && pos < e) dl[i] = (int)(doc - doc0);
+          if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
+          else x[i] = (AccT)load_x<IMPACT>(blk, lane);
         }
-      } else {
-        const float x = load_x<IMPACT>(blk, lane);
-        for (int32_t en = eb; en < ee; ++en) {
-          const uint2 E = __ldg(ent + en);
-          if (valid) atomicAdd(reinterpret_cast<float*>(acc) + E.x * T + dl, __uint_as_float(E.y) * x);
+      }
+      const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+      const int32_t eb = s_e0[jj], ee = s_e1[jj];
+#pragma unroll 2
+      for (int32_t en = eb; en < ee; ++en) {
+        const uint2 E = E_ptr[en - ent_lo];
+        const uint32_t row = acc_s + (E.x * (uint32_t)T) * 4u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (dl[i] >= 0) {
+            const uint32_t addr = row + (uint32_t)dl[i] * 4u;
+            if (IMPACT == GS_IMPACT_U8) {
+              const int32_t v = (int32_t)E.y * (int32_t)x[i];
+              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+            } else {
+              const float v = __uint_as_float(E.y) * (float)x[i];
+              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+            }
+          }
         }
       }
     }
@@ -507,7 +552,7 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
 template <int IMPACT>
 gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
                        const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
-  const size_t smem = (size_t)c.G * c.T * 4;
+  const size_t smem = (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + kItemCap * sizeof(uint16_t);
   auto ks = dt_tile_kernel<IMPACT, kModeSample>;
   auto km = dt_tile_kernel<IMPACT, kModeMain>;
   GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
