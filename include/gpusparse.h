@@ -104,11 +104,18 @@ typedef enum {
 
 typedef struct gs_index gs_index;
 
+#define GS_MAX_HEAD_TERMS 64
+
 typedef struct {
-  int32_t tile_docs; /* documents per tile of the segment table used by the
-                        doc-tiled kernel: a power of two in [256, 65536];
-                        0 = default (1024); -1 = build no table */
-  int32_t reserved[7];
+  int32_t tile_docs;  /* documents per tile of the segment table used by the
+                         doc-tiled kernel: a power of two in [256, 65536];
+                         0 = default (1024); -1 = build no table */
+  int32_t head_terms; /* dense head: the H terms with the longest posting
+                         lists also get a dense [H x N] impact matrix that the
+                         doc-tiled kernel multiplies with FMAs instead of
+                         scattering them; 0 = default (32), -1 = none,
+                         at most GS_MAX_HEAD_TERMS */
+  int32_t reserved[6];
 } gs_build_opts;
 
 typedef struct {
@@ -124,6 +131,9 @@ typedef struct {
   int32_t tile_docs;        /* 0 when no tile table was built */
   int32_t num_tiles;
   int32_t score_is_int;     /* 1 on the U8 path: scores are int32 */
+  int32_t head_terms;       /* H of the dense head (0: none) */
+  int32_t reserved0;
+  int64_t head_bytes;       /* bytes of the dense head matrix */
 } gs_index_stats;
 
 /* Read-only views of the index's device arrays (for inspection and tests).
@@ -136,6 +146,9 @@ typedef struct {
   const int32_t* term_len;    /* [vocab] postings of each list, unpadded */
   const float* max_score;     /* [vocab] largest stored impact of each list */
   const uint32_t* seg;        /* see above; NULL without a tile table */
+  const int32_t* head_term;   /* [head_terms] term ids of the dense head */
+  const void* head_dense;     /* [head_terms][head_ld] impacts (index type) */
+  int64_t head_ld;            /* row length of head_dense, >= num_docs */
 } gs_index_layout;
 
 /* Stage boundaries at which gs_search records the caller's CUDA events when
@@ -154,7 +167,8 @@ typedef struct {
   int32_t sample_stride; /* DOC_TILED: 1 of every R tiles forms the threshold
                             sample (0 = auto, 1 = no sampling: every
                             document is a candidate) */
-  int32_t reserved;
+  int32_t use_head;      /* DOC_TILED: 0 = use the index's dense head when it
+                            has one (requires 32 queries per group), -1 = off */
   void* const* stage_events; /* NULL, or GS_NUM_STAGE_EVENTS cudaEvent_t */
 } gs_search_opts;
 
@@ -237,7 +251,9 @@ typedef struct {
   int32_t sample_tiles;  /* tiles j * R, j < sample_tiles, form the sample */
   int32_t chunk_blocks;  /* TERM_PARALLEL: blocks per work item */
   int64_t cand_capacity; /* DOC_TILED: candidate slots per query */
-  int64_t reserved[4];
+  int32_t head_terms;    /* DOC_TILED: dense head terms used (0: none) */
+  int32_t reserved0;
+  int64_t reserved[3];
 } gs_plan_info;
 
 gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,

@@ -36,11 +36,14 @@ constexpr int kDtThreads = 1024;
 constexpr int kDtMaxAccBytes = 128 * 1024;  // G x T accumulators
 constexpr int kEntCap = 4096;                // query entries staged in shared memory (32 KB)
 constexpr int kItemCap = 9216;               // (term, 128-posting chunk) items per term batch (18 KB)
+constexpr int kMaxGroup = 256;               // queries per group (thresholds kept in shared memory)
+constexpr int kHeadG = 32;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 32;
 constexpr int kDefaultSampleStride = 16;
 
 struct DtConfig {
   int G = 0, T = 0, m = 0, R = 0;  // R = 0: no sampling
+  int H = 0;                        // dense head terms used (0: none)
   int ng = 0, nt = 0, n_sample = 0;
   int64_t sample_docs = 0;
   int64_t cap = 0;
@@ -53,7 +56,10 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   if (c->T % ix->tile_docs != 0) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
-  G = std::min(G, B);
+  // the dense head keeps one accumulator register per query of the group
+  const bool head = ix->head_H > 0 && !(opts && opts->use_head < 0) && G == kHeadG;
+  c->H = head ? ix->head_H : 0;
+  G = head ? kHeadG : std::min(std::min(G, B), kMaxGroup);
   if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {
     if (opts && opts->group_queries > 0) return GS_ERR_INVALID_ARG;
     G = std::max(1, kDtMaxAccBytes / (c->T * 4));
@@ -89,6 +95,9 @@ struct DtPlan {
   uint2* cand;        // [B][cap] (key, doc)
   uint32_t* cand_cnt; // [B]
   uint32_t* tiebm;    // [B][bm_words]
+  uint32_t* headw;    // [ng][H][kHeadG] head weights (float or int bits)
+  int32_t* head_act;  // [ng][H] head rows with a non-zero weight
+  int32_t* head_nact; // [ng]
 };
 
 DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const DtConfig& c, size_t* bytes) {
@@ -105,6 +114,9 @@ DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const
   p.cand = cv.take<uint2>((size_t)B * c.cap);
   p.cand_cnt = cv.take<uint32_t>(B);
   p.tiebm = cv.take<uint32_t>((size_t)B * c.bm_words);
+  p.headw = cv.take<uint32_t>((size_t)c.ng * std::max(c.H, 1) * kHeadG);
+  p.head_act = cv.take<int32_t>((size_t)c.ng * std::max(c.H, 1));
+  p.head_nact = cv.take<int32_t>(c.ng);
   *bytes = cv.size();
   return p;
 }
@@ -127,7 +139,9 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
                                                        int impact, uint32_t* __restrict__ cnt_all,
                                                        int32_t* __restrict__ u_terms, int32_t* __restrict__ u_ptr,
                                                        int32_t* __restrict__ n_u, uint2* __restrict__ ent,
-                                                       uint32_t* flags) {
+                                                       const int32_t* __restrict__ head_slot, int H,
+                                                       uint32_t* __restrict__ headw, int32_t* __restrict__ head_act,
+                                                       int32_t* __restrict__ head_nact, uint32_t* flags) {
   __shared__ int warp_buf[32];
   const int g = blockIdx.x;
   const int q0 = g * G, q1 = min(B, q0 + G);
@@ -141,12 +155,21 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
   const int32_t e1 = min(max(q_indptr[q1], e0), q_nnz);
   uint32_t* cnt = cnt_all + (int64_t)g * V;
   for (int t = threadIdx.x; t < V; t += blockDim.x) cnt[t] = 0u;
+  uint32_t* hw = headw + (int64_t)g * H * kHeadG;
+  for (int i = threadIdx.x; i < H * kHeadG; i += blockDim.x) hw[i] = 0u;
   __syncthreads();
   for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int32_t t = q_terms[e];
     const float w = q_w[e];
     if (t < 0 || t >= V) { fl |= kFlagBadTerm; continue; }
     if (!isfinite(w)) { fl |= kFlagBadWeight; continue; }
+    if (H > 0 && __ldg(head_slot + t) >= 0) {  // a head term: dense weight row
+      const int ql = min(max(ub_i32(q_indptr + q0, q1 - q0 + 1, e) - 1, 0), q1 - q0 - 1);
+      uint32_t* slotp = hw + (int64_t)__ldg(head_slot + t) * kHeadG + ql;
+      if (impact == GS_IMPACT_U8) atomicAdd(reinterpret_cast<int32_t*>(slotp), quant_u8(w));
+      else atomicAdd(reinterpret_cast<float*>(slotp), w);
+      continue;
+    }
     atomicAdd(&cnt[t], 1u);
   }
   __syncthreads();
@@ -176,10 +199,22 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
     const int32_t t = q_terms[e];
     const float w = q_w[e];
     if (t < 0 || t >= V || !isfinite(w)) continue;
+    if (H > 0 && __ldg(head_slot + t) >= 0) continue;
     const int ql = min(max(ub_i32(q_indptr + q0, q1 - q0 + 1, e) - 1, 0), q1 - q0 - 1);
     const uint32_t pos = atomicAdd(&cnt[t], 1u);
     const uint32_t wb = impact == GS_IMPACT_U8 ? (uint32_t)quant_u8(w) : __float_as_uint(w);
     ent[pos] = make_uint2((uint32_t)ql, wb);
+  }
+  // head rows some query of the group uses
+  if (H > 0) {
+    __syncthreads();
+    int used = 0;
+    if ((int)threadIdx.x < H)
+      for (int q = 0; q < kHeadG; ++q) used |= __ldcg(hw + threadIdx.x * kHeadG + q) != 0u;
+    int tot;
+    const int x = block_excl_scan(used, warp_buf, &tot);
+    if (used) head_act[(int64_t)g * H + x] = (int32_t)threadIdx.x;
+    if (threadIdx.x == 0) head_nact[g] = tot;
   }
   if (fl) atomicOr(flags, fl);
 }
@@ -205,7 +240,14 @@ __device__ __forceinline__ uint32_t theta_key(const uint32_t* samp_sc, int64_t q
 }
 
 // One CTA per (tile, group): G x T score block in shared memory.
-template <int IMPACT, int MODE>
+//
+// Work items are (term, chunk of 4 posting blocks = 128 postings) pairs of
+// the group's distinct terms, handed out dynamically to the 32 warps.  Lane l
+// of a warp takes posting l of each of the 4 blocks, so the 32 lanes of one
+// reduction address 32 distinct documents of one query row (consecutive
+// documents for dense terms: no bank conflicts), and every loaded posting
+// serves all of the group's queries holding the term.
+template <int IMPACT, int MODE, bool HEAD>
 __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const uint32_t* __restrict__ seg,
     int seg_tiles, int64_t N, const int32_t* __restrict__ q_indptr, int32_t B, int32_t q_nnz, int G, int T,
@@ -213,7 +255,9 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     int ng, int n_sample, const int32_t* __restrict__ u_terms, const int32_t* __restrict__ u_ptr,
     const int32_t* __restrict__ n_u, const uint2* __restrict__ ent, uint32_t* __restrict__ samp,
     int64_t sample_docs, const uint32_t* __restrict__ samp_sc, int k, uint2* __restrict__ cand,
-    uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words) {
+    uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
+    const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
+    const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
   // dynamic shared memory: [G x T accumulators][staged query entries][item -> term]
@@ -221,10 +265,12 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
   uint2* ent_s = reinterpret_cast<uint2*>(dyn_smem + (size_t)G * T * sizeof(AccT));
   uint16_t* item_term = reinterpret_cast<uint16_t*>(ent_s + kEntCap);
-  __shared__ uint32_t s_start[kDtThreads], s_end[kDtThreads];
+  __shared__ const uint8_t* s_p0[kDtThreads];  // first block of the term's segment
+  __shared__ int32_t s_off[kDtThreads];         // segment start within that block
+  __shared__ int32_t s_len[kDtThreads];         // postings in the segment
   __shared__ int32_t s_item[kDtThreads + 1];
-  __shared__ int64_t s_blk0[kDtThreads];
   __shared__ int32_t s_e0[kDtThreads], s_e1[kDtThreads];
+  __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
   __shared__ int s_next;
 
@@ -246,18 +292,25 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     uint4* a4 = reinterpret_cast<uint4*>(acc);
     for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
   }
+  if (MODE == kModeMain)
+    for (int i = threadIdx.x; i < gq; i += blockDim.x)
+      s_theta[i] = R > 0 ? __ldg(samp_sc + (int64_t)(q0 + i) * k + (k - 1)) : 0u;
   const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
   const int nterm = n_u[g];
   const int32_t* ut = u_terms + ebase;
   const int32_t* up = u_ptr + ebase + g;
   const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
-  // the group's (query, weight) entries, staged in shared memory when they fit
+  // the group's (query, weight) entries, staged with the query's row byte offset
   const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
   const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
   const bool staged = (ent_hi - ent_lo) <= kEntCap;
+  const uint32_t row_bytes = (uint32_t)T * 4u;
   if (staged)
-    for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) ent_s[i] = __ldg(ent + ent_lo + i);
-  const uint2* E_ptr = staged ? ent_s : ent + ent_lo;  // indexed by entry position - ent_lo
+    for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) {
+      const uint2 E = __ldg(ent + ent_lo + i);
+      ent_s[i] = make_uint2(E.x * row_bytes, E.y);
+    }
+  const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
   // terms per batch: their 128-posting work items must fit the item table
   const int items_per_term = T / 128 + 1;
   const int tb = min(kDtThreads, kItemCap / items_per_term);
@@ -270,9 +323,9 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       const int32_t t = ut[j];
       const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
       const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
-      s_start[threadIdx.x] = s;
-      s_end[threadIdx.x] = e;
-      s_blk0[threadIdx.x] = __ldg(term_block + t) + (s >> 5);
+      s_p0[threadIdx.x] = blocks + (__ldg(term_block + t) + (int64_t)(s >> 5)) * bb;
+      s_off[threadIdx.x] = (int32_t)(s & 31u);
+      s_len[threadIdx.x] = (int32_t)(e - s);
       s_e0[threadIdx.x] = __ldg(up + j);
       s_e1[threadIdx.x] = __ldg(up + j + 1);
       if (e > s) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
@@ -283,7 +336,6 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    // dynamic work distribution over (term, 4-block chunk) items
     int nxt = 0;
     if (lane == 0) nxt = atomicAdd(&s_next, 1);
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
@@ -293,42 +345,42 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       nxt = __shfl_sync(0xffffffffu, nxt, 0);
       const int jj = item_term[it];
       const int c = it - s_item[jj];
-      const uint32_t s = s_start[jj], e = s_end[jj];
-      const uint32_t fb = (s >> 5) + 4u * (uint32_t)c;  // first block of the chunk (list-relative)
-      const uint32_t lb = (e - 1) >> 5;                // last block of the segment
-      const uint8_t* base = blocks + (s_blk0[jj] + 4 * c) * bb;
-      int dl[4];
+      const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
+      const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
+      const uint32_t len = (uint32_t)s_len[jj];
+      int da[4];  // byte offset of the document inside a row, -1 when the lane has no posting
       AccT x[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        dl[i] = -1;
+        da[i] = -1;
         x[i] = (AccT)0;
-        const uint32_t b = fb + (uint32_t)i;
-        if (b <= lb) {
+        if ((uint32_t)(rel + 32 * i) < len) {
           const uint8_t* blk = base + i * bb;
-          const uint32_t pos = b * 32u + (uint32_t)lane;
           const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
-          if (pos >= s && pos < e) dl[i] = (int)(doc - doc0);
+          da[i] = (int)(doc - doc0) * 4;
           if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
           else x[i] = (AccT)load_x<IMPACT>(blk, lane);
         }
       }
-      const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
       const int32_t eb = s_e0[jj], ee = s_e1[jj];
-#pragma unroll 2
       for (int32_t en = eb; en < ee; ++en) {
-        const uint2 E = E_ptr[en - ent_lo];
-        const uint32_t row = acc_s + (E.x * (uint32_t)T) * 4u;
+        uint2 E;
+        if (staged) {
+          E = ent_s[en - ent_lo];
+        } else {
+          E = __ldg(ent + en);
+          E.x *= row_bytes;
+        }
+        const uint32_t row = acc_s + E.x;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          if (dl[i] >= 0) {
-            const uint32_t addr = row + (uint32_t)dl[i] * 4u;
+          if (da[i] >= 0) {
+            const uint32_t addr = row + (uint32_t)da[i];
             if (IMPACT == GS_IMPACT_U8) {
-              const int32_t v = (int32_t)E.y * (int32_t)x[i];
-              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)E.y * (int32_t)x[i]) : "memory");
             } else {
-              const float v = __uint_as_float(E.y) * (float)x[i];
-              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(E.y) * (float)x[i])
+                           : "memory");
             }
           }
         }
@@ -337,37 +389,110 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     __syncthreads();
   }
 
-  if (MODE == kModeSample) {
-    // dense sample rows: samp[q][tile_idx * T + d]
-    for (int i = threadIdx.x; i < gq * T; i += blockDim.x) {
-      const int ql = i / T, d = i - ql * T;
-      const AccT v = acc[ql * T + d];
-      uint32_t bits;
-      memcpy(&bits, &v, 4);
-      samp[(int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d] = bits;
+  if (HEAD) {
+    // dense head: S[q][d] += sum_h W[q][h] * X[h][d] with one accumulator
+    // register per query (thread = document), weights broadcast from shared
+    // memory; every (query, document) cell is owned by one thread
+    __shared__ __align__(16) AccT s_w[GS_MAX_HEAD_TERMS * kHeadG];
+    __shared__ int32_t s_hact[GS_MAX_HEAD_TERMS];
+    const int nact = head_nact[g];
+    for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
+      const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
+      memcpy(&s_w[i], &raw, 4);
     }
-  } else {
-    // candidates above theta_q, ties in the bitmap
-    for (int c0 = warp * 32; c0 < gq * T; c0 += kDtThreads) {
-      const int i = c0 + lane;
-      const int ql = i / T, d = i - ql * T;  // T is a multiple of 32: one row per warp step
-      const int q = q0 + ql;
-      const int64_t doc = doc0 + d;
-      const uint32_t theta = theta_key<AccT>(samp_sc, q, k, R);
-      const uint32_t key = score_key(acc[ql * T + d]);
-      const bool in = doc < N;
-      const bool gt = in && key > theta;
-      const bool tie = in && key == theta;
-      const unsigned mgt = __ballot_sync(0xffffffffu, gt);
-      const unsigned mtie = __ballot_sync(0xffffffffu, tie);
-      if (doc0 + (c0 - ql * T) < N && lane == 0) tiebm[(int64_t)q * bm_words + ((doc0 + (c0 - ql * T)) >> 5)] = mtie;
-      if (mgt) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)__popc(mgt));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (gt) {
-          const uint32_t slot = base + (uint32_t)__popc(mgt & ((1u << lane) - 1u));
-          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(key, (uint32_t)doc);
+    __syncthreads();
+    for (int d = threadIdx.x; d < T; d += blockDim.x) {
+      AccT r[kHeadG];
+#pragma unroll
+      for (int q = 0; q < kHeadG; ++q) r[q] = (AccT)0;
+      const int64_t col = doc0 + d;
+      for (int a = 0; a < nact; ++a) {
+        const int64_t at = (int64_t)s_hact[a] * head_ld + col;
+        AccT x;
+        if (IMPACT == GS_IMPACT_F32) x = __ldg(reinterpret_cast<const float*>(head_dense) + at);
+        else if (IMPACT == GS_IMPACT_F16) x = __half2float(__ldg(reinterpret_cast<const __half*>(head_dense) + at));
+        else if (IMPACT == GS_IMPACT_BF16)
+          x = __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(head_dense) + at));
+        else x = (AccT)__ldg(head_dense + at);
+        const AccT* wr = s_w + a * kHeadG;
+#pragma unroll
+        for (int q4 = 0; q4 < kHeadG / 4; ++q4) {
+          AccT w4[4];
+          *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (IMPACT == GS_IMPACT_U8) r[4 * q4 + u] += w4[u] * x;
+            else r[4 * q4 + u] = fmaf((float)w4[u], (float)x, (float)r[4 * q4 + u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kHeadG; ++q)
+        if (q < gq) acc[q * T + d] += r[q];
+    }
+    __syncthreads();
+  }
+
+  // epilogue: each warp step covers 128 documents of one query row (4 per lane)
+  const int cpr = T / 128;  // chunks per row
+  for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
+    const int ql = ci / cpr;
+    const int d0 = (ci - ql * cpr) * 128 + lane * 4;
+    const uint4 raw = *reinterpret_cast<const uint4*>(acc + ql * T + d0);
+    if (MODE == kModeSample) {
+      *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) = raw;
+      continue;
+    }
+    const int q = q0 + ql;
+    const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+    const uint32_t th = s_theta[ql];
+    unsigned gtm = 0, eqm = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool in = doc0 + d0 + i < N;
+      bool gt, eq;
+      if (R <= 0) {
+        gt = in;
+        eq = false;
+      } else if (IMPACT == GS_IMPACT_U8) {
+        gt = in && (int32_t)rv[i] > (int32_t)th;
+        eq = in && (int32_t)rv[i] == (int32_t)th;
+      } else {
+        gt = in && __uint_as_float(rv[i]) > __uint_as_float(th);
+        eq = in && __uint_as_float(rv[i]) == __uint_as_float(th);
+      }
+      gtm |= (unsigned)gt << i;
+      eqm |= (unsigned)eq << i;
+    }
+    // tie bitmap: 8 lanes x 4 documents make one 32-bit word
+    unsigned word = eqm << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    const int64_t wdoc = doc0 + (d0 - (lane & 7) * 4);
+    if ((lane & 7) == 0 && wdoc < N) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+    if (__any_sync(0xffffffffu, gtm != 0)) {
+      const int cnt = __popc(gtm);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      uint32_t basec = 0;
+      if (lane == 0) basec = atomicAdd(&cand_cnt[q], (uint32_t)tot);
+      basec = __shfl_sync(0xffffffffu, basec, 0);
+      uint32_t slot = basec + (uint32_t)(incl - cnt);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (gtm & (1u << i)) {
+          AccT v;
+          memcpy(&v, &rv[i], 4);
+          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(v), (uint32_t)(doc0 + d0 + i));
+          ++slot;
         }
       }
     }
@@ -549,20 +674,20 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   }
 }
 
-template <int IMPACT>
-gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
-                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
+template <int IMPACT, bool HEAD>
+gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
+                         const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
   const size_t smem = (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + kItemCap * sizeof(uint16_t);
-  auto ks = dt_tile_kernel<IMPACT, kModeSample>;
-  auto km = dt_tile_kernel<IMPACT, kModeMain>;
+  auto ks = dt_tile_kernel<IMPACT, kModeSample, HEAD>;
+  auto km = dt_tile_kernel<IMPACT, kModeMain, HEAD>;
   GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GS_CUDA_TRY(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (c.R > 0) {
     ks<<<c.n_sample * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N,
                                                    q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample,
-                                                   p.u_terms,
-                                                   p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.samp_sc, k,
-                                                   p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words);
+                                                   p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.samp_sc,
+                                                   k, p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->head_dense,
+                                                   ix->head_ld, c.H, p.headw, p.head_act, p.head_nact);
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
@@ -579,12 +704,20 @@ gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32
   }
   record_stage(opts, 3, s);
   km<<<c.nt * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B,
-                                           q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent,
-                                           p.samp, c.sample_docs, p.samp_sc, k, p.cand, p.cand_cnt, c.cap,
-                                           p.tiebm, c.bm_words);
+                                           q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u,
+                                           p.ent, p.samp, c.sample_docs, p.samp_sc, k, p.cand, p.cand_cnt, c.cap,
+                                           p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act,
+                                           p.head_nact);
   GS_LAUNCH_CHECK();
   record_stage(opts, 4, s);
   return GS_OK;
+}
+
+template <int IMPACT>
+gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
+                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
+  if (c.H > 0) return launch_tiles_h<IMPACT, true>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
+  return launch_tiles_h<IMPACT, false>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
 }
 
 }  // namespace
@@ -601,6 +734,7 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
   out->num_tiles = c.nt;
   out->sample_tiles = c.n_sample;
   out->cand_capacity = c.cap;
+  out->head_terms = c.H;
   return GS_OK;
 }
 
@@ -623,8 +757,9 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   DtPlan p = carve_dt(ws, ix, B, q_nnz, k, c, &need);
   if (need > ws_bytes) return GS_ERR_WORKSPACE;
   record_stage(opts, 0, s);
-  dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt, p.u_terms, p.u_ptr,
-                                       p.n_u, p.ent, flags);
+  dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt,
+                                       p.u_terms, p.u_ptr, p.n_u, p.ent, ix->head_slot, c.H, p.headw, p.head_act,
+                                       p.head_nact, flags);
   GS_LAUNCH_CHECK();
   GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
   record_stage(opts, 1, s);

@@ -220,6 +220,26 @@ __global__ void finalize_kernel(const uint8_t* __restrict__ blocks, const int64_
   if (e) atomicOr(err, e);
 }
 
+// Dense head: row h holds, for every document, the stored impact of term
+// head_term[h] (0 where the document lacks it).  One CTA per head term.
+__global__ void head_fill_kernel(const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block,
+                                 const int32_t* __restrict__ term_len, const int32_t* __restrict__ head_term,
+                                 int impact, int64_t head_ld, uint8_t* __restrict__ head_dense) {
+  const int h = blockIdx.x;
+  const int32_t t = head_term[h];
+  const int ib = impact_bytes(impact);
+  const int bb = block_bytes(impact);
+  const uint8_t* base = blocks + term_block[t] * bb;
+  uint8_t* row = head_dense + (int64_t)h * head_ld * ib;
+  for (int64_t p = threadIdx.x; p < term_len[t]; p += blockDim.x) {
+    const uint8_t* blk = base + (p / kBlock) * bb;
+    const int li = (int)(p % kBlock);
+    const int32_t doc = reinterpret_cast<const int32_t*>(blk)[li];
+    if (doc < 0 || doc >= head_ld) continue;  // only valid lists reach here; stay in bounds regardless
+    for (int b = 0; b < ib; ++b) row[(int64_t)doc * ib + b] = blk[128 + li * ib + b];
+  }
+}
+
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
@@ -261,6 +281,9 @@ static void free_index(gs_index* ix) {
   cudaFree(ix->term_len);
   cudaFree(ix->max_score);
   cudaFree(ix->seg);
+  cudaFree(ix->head_term);
+  cudaFree(ix->head_slot);
+  cudaFree(ix->head_dense);
   delete ix;
 }
 
@@ -277,6 +300,10 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
   if (opts && opts->tile_docs != 0) tile_docs = opts->tile_docs;
   if (tile_docs != -1 && (tile_docs < 256 || tile_docs > 65536 || (tile_docs & (tile_docs - 1))))
     return GS_ERR_INVALID_ARG;
+  int head_req = 32;
+  if (opts && opts->head_terms != 0) head_req = opts->head_terms;
+  if (head_req < -1 || head_req > GS_MAX_HEAD_TERMS) return GS_ERR_INVALID_ARG;
+  if (head_req < 0 || tile_docs < 0) head_req = 0;  // the head serves the doc-tiled kernel only
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
   gs_index* ix = new gs_index();
@@ -400,6 +427,42 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
     return cuda_fail(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
   if (herr) return fail(GS_ERR_DATA);
+  // dense head: the head_req longest lists (ties: lower term id)
+  if (head_req > 0) {
+    std::vector<int32_t> order(vocab);
+    for (int32_t t = 0; t < vocab; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return ix->h_term_len[a] > ix->h_term_len[b]; });
+    int H = 0;
+    while (H < head_req && H < vocab && ix->h_term_len[order[H]] > 0) ++H;
+    if (H > 0) {
+      ix->head_H = H;
+      ix->head_ld = (num_docs + 65535) / 65536 * 65536;  // every tile of every size reads in bounds
+      std::vector<int32_t> slot(vocab, -1);
+      for (int h = 0; h < H; ++h) slot[order[h]] = h;
+      const size_t hbytes = (size_t)H * ix->head_ld * impact_bytes(impact);
+      if ((e = cudaMalloc(&ix->head_term, sizeof(int32_t) * H)) != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaMalloc(&ix->head_slot, sizeof(int32_t) * vocab)) != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaMalloc(&ix->head_dense, hbytes)) != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaMemcpyAsync(ix->head_term, order.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e);
+      if ((e = cudaMemcpyAsync(ix->head_slot, slot.data(), sizeof(int32_t) * vocab, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e);
+      if ((e = cudaMemsetAsync(ix->head_dense, 0, hbytes, s)) != cudaSuccess) return cuda_fail(e);
+      head_fill_kernel<<<H, 512, 0, s>>>(ix->blocks, ix->term_block, ix->term_len, ix->head_term, impact,
+                                         ix->head_ld, ix->head_dense);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+      ix->meta_bytes += (int64_t)(sizeof(int32_t) * (H + vocab));
+      // the host copies must outlive the asynchronous uploads
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  if ((e = cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+  if (herr) return fail(GS_ERR_DATA);
   *out = ix;
   return GS_OK;
 }
@@ -425,6 +488,8 @@ extern "C" gs_status gs_index_info(const gs_index* ix, gs_index_stats* out) {
   out->tile_docs = ix->tile_docs;
   out->num_tiles = ix->num_tiles;
   out->score_is_int = ix->impact == GS_IMPACT_U8 ? 1 : 0;
+  out->head_terms = ix->head_H;
+  out->head_bytes = (int64_t)ix->head_H * ix->head_ld * impact_bytes(ix->impact);
   return GS_OK;
 }
 
@@ -435,6 +500,9 @@ extern "C" gs_status gs_index_get_layout(const gs_index* ix, gs_index_layout* ou
   out->term_len = ix->term_len;
   out->max_score = ix->max_score;
   out->seg = ix->seg;
+  out->head_term = ix->head_term;
+  out->head_dense = ix->head_dense;
+  out->head_ld = ix->head_ld;
   return GS_OK;
 }
 

@@ -45,6 +45,12 @@ struct gs_index {
   int32_t* term_len = nullptr;     // V
   float* max_score = nullptr;      // V
   uint32_t* seg = nullptr;         // V * (num_tiles + 1)
+  // dense head: the H longest lists as an [H][head_ld] impact matrix
+  int32_t head_H = 0;
+  int64_t head_ld = 0;
+  int32_t* head_term = nullptr;    // H
+  int32_t* head_slot = nullptr;    // V, -1 outside the head
+  uint8_t* head_dense = nullptr;   // H * head_ld * impact_bytes
   int64_t meta_bytes = 0;
   // host copies for planning
   std::vector<int64_t> h_term_block;

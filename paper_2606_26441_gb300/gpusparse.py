@@ -44,32 +44,35 @@ class GsError(RuntimeError):
 
 
 class gs_build_opts(ctypes.Structure):
-    _fields_ = [("tile_docs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("tile_docs", ctypes.c_int32), ("head_terms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class gs_index_stats(ctypes.Structure):
     _fields_ = [("num_docs", ctypes.c_int64), ("postings", ctypes.c_int64), ("padded_postings", ctypes.c_int64),
                 ("blocks", ctypes.c_int64), ("posting_bytes", ctypes.c_int64), ("meta_bytes", ctypes.c_int64),
                 ("vocab", ctypes.c_int32), ("impact", ctypes.c_int32), ("block_bytes", ctypes.c_int32),
-                ("tile_docs", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("score_is_int", ctypes.c_int32)]
+                ("tile_docs", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("score_is_int", ctypes.c_int32),
+                ("head_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("head_bytes", ctypes.c_int64)]
 
 
 class gs_index_layout(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_void_p), ("term_block", ctypes.c_void_p), ("term_len", ctypes.c_void_p),
-                ("max_score", ctypes.c_void_p), ("seg", ctypes.c_void_p)]
+                ("max_score", ctypes.c_void_p), ("seg", ctypes.c_void_p), ("head_term", ctypes.c_void_p),
+                ("head_dense", ctypes.c_void_p), ("head_ld", ctypes.c_int64)]
 
 
 class gs_search_opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
                 ("chunk_blocks", ctypes.c_int32), ("sample_stride", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p))]
+                ("use_head", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p))]
 
 
 class gs_plan_info(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
                 ("sample_stride", ctypes.c_int32), ("num_groups", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("sample_tiles", ctypes.c_int32), ("chunk_blocks", ctypes.c_int32),
-                ("cand_capacity", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+                ("cand_capacity", ctypes.c_int64), ("head_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 _lib = None
@@ -136,13 +139,14 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0,
+def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0, use_head=0,
               stage_events=None) -> gs_search_opts:
     """stage_events: None or GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
     o = gs_search_opts()
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.group_queries, o.tile_docs = group_queries, tile_docs
     o.chunk_blocks, o.sample_stride = chunk_blocks, sample_stride
+    o.use_head = use_head
     if stage_events is not None:
         assert len(stage_events) == GS_NUM_STAGE_EVENTS
         arr = (ctypes.c_void_p * GS_NUM_STAGE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in stage_events])
@@ -182,8 +186,8 @@ class Index:
 
     @staticmethod
     def build(doc_indptr: torch.Tensor, doc_terms: torch.Tensor, doc_w: torch.Tensor, vocab: int,
-              impact: str = "f32", tile_docs: int = 0, stream=None) -> "Index":
-        return gs_index_build(doc_indptr, doc_terms, doc_w, vocab, impact, tile_docs, stream)
+              impact: str = "f32", tile_docs: int = 0, head_terms: int = 0, stream=None) -> "Index":
+        return gs_index_build(doc_indptr, doc_terms, doc_w, vocab, impact, tile_docs, head_terms, stream)
 
     @property
     def handle(self):
@@ -237,13 +241,14 @@ class Index:
 
 
 def gs_index_build(doc_indptr, doc_terms, doc_w, vocab: int, impact: str = "f32", tile_docs: int = 0,
-                   stream=None) -> Index:
+                   head_terms: int = 0, stream=None) -> Index:
     """Builds the index from device CSR tensors (int64 indptr, int32 terms, float32 weights)."""
     L = load()
     assert doc_indptr.dtype == torch.int64 and doc_terms.dtype == torch.int32 and doc_w.dtype == torch.float32
     h = ctypes.c_void_p()
     o = gs_build_opts()
     o.tile_docs = tile_docs
+    o.head_terms = head_terms
     _check(L.gs_index_build_ex(_ptr(doc_indptr), _ptr(doc_terms), _ptr(doc_w), doc_indptr.numel() - 1,
                                doc_terms.numel(), vocab, IMPACTS[impact], ctypes.byref(o), _stream(stream),
                                ctypes.byref(h)), "gs_index_build")

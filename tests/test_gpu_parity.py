@@ -16,6 +16,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ALGOS = ["term_parallel", "doc_tiled"]
+# the doc-tiled kernel with and without the dense head
+VARIANTS = [("term_parallel", {}), ("doc_tiled", {}), ("doc_tiled", {"use_head": -1})]
 
 
 def _gs():
@@ -47,12 +49,13 @@ def _cudart():
 class Case:
     """A collection + query batch + GPU index + oracle index for one impact type."""
 
-    def __init__(self, docs, qs, impact, tile_docs=0):
+    def __init__(self, docs, qs, impact, tile_docs=0, head_terms=0):
         gs = _gs()
         dev = _dev()
         self.docs, self.qs, self.impact = docs, qs, impact
         self.idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
-                                     torch.from_numpy(docs.weights).to(dev), docs.vocab, impact, tile_docs)
+                                     torch.from_numpy(docs.weights).to(dev), docs.vocab, impact, tile_docs,
+                                     head_terms)
         self.q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
         self.ref = oracle.OracleIndex.from_batch(docs, impact)
 
@@ -87,20 +90,46 @@ def cases(tiny_docs):
     return {imp: Case(docs, qs, imp) for imp in ("f32", "f16", "bf16", "u8")}
 
 
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo,kw", VARIANTS)
 @pytest.mark.parametrize("impact", ["f32", "f16", "bf16", "u8"])
-def test_topk_small_workload(cases, impact, algo):
-    stats = cases[impact].check(10, algo)
+def test_topk_small_workload(cases, impact, algo, kw):
+    stats = cases[impact].check(10, algo, **kw)
     if stats:
         assert stats["max_rel_err"] < 1e-5
 
 
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo,kw", VARIANTS)
 @pytest.mark.parametrize("impact", ["f32", "u8"])
-def test_topk_k1000_and_kmax(cases, impact, algo):
-    cases[impact].check(1000, algo)
-    cases[impact].check(2048, algo)
-    cases[impact].check(1, algo)
+def test_topk_k1000_and_kmax(cases, impact, algo, kw):
+    cases[impact].check(1000, algo, **kw)
+    cases[impact].check(2048, algo, **kw)
+    cases[impact].check(1, algo, **kw)
+
+
+def test_dense_head_layout(cases):
+    """The dense head holds, for the longest lists, every document's stored impact (0 if absent)."""
+    for impact in ("f32", "u8"):
+        c = cases[impact]
+        st = c.idx.stats()
+        lay = c.idx.layout()
+        assert st.head_terms == 32
+        H, ld = st.head_terms, lay.head_ld
+        ib = {"f32": 4, "u8": 1}[impact]
+        torch.cuda.synchronize()
+        ht = np.empty(H, np.int32)
+        assert _cudart().cudaMemcpy(ctypes.c_void_p(ht.ctypes.data), ctypes.c_void_p(lay.head_term), 4 * H, 2) == 0
+        dense = np.empty(H * ld * ib, np.uint8)
+        assert _cudart().cudaMemcpy(ctypes.c_void_p(dense.ctypes.data), ctypes.c_void_p(lay.head_dense),
+                                    dense.nbytes, 2) == 0
+        dense = (dense.view(np.float32) if impact == "f32" else dense).reshape(H, ld).astype(np.float64)
+        lens = [len(c.ref.posting_list(int(t))[0]) for t in range(c.docs.vocab)]
+        order = sorted(range(c.docs.vocab), key=lambda t: (-lens[t], t))[:H]
+        assert ht.tolist() == order
+        for h in range(H):
+            docs_t, x_t = c.ref.posting_list(int(ht[h]))
+            row = np.zeros(ld)
+            row[docs_t] = x_t
+            assert np.array_equal(dense[h], row)
 
 
 @pytest.mark.parametrize("impact", ["f32", "u8"])
@@ -187,9 +216,9 @@ def test_edge_cases():
                            np.array(sum([list(r[1]) for r in rows], []), np.float32))
     for impact in ("u8", "f32"):
         c = Case(docs, qs, impact, tile_docs=256)
-        for algo in ALGOS:
+        for algo, kw in VARIANTS:
             for k in (1, 7, 300, 2048):
-                c.check(k, algo)
+                c.check(k, algo, **kw)
     # a single query
     single = qs.slice(3, 4)
     c = Case(docs, single, "f32", tile_docs=256)
@@ -269,6 +298,6 @@ def test_medium_workload_1m():
     qs = synth.queries(128, seed=0)
     for impact in ("u8", "f32"):
         c = Case(docs, qs, impact)
-        for algo in ALGOS:
-            c.check(1000, algo)
+        for algo, kw in VARIANTS:
+            c.check(1000, algo, **kw)
         c.idx.free()
