@@ -34,8 +34,10 @@ namespace {
 
 constexpr int kDtThreads = 1024;
 constexpr int kDtMaxAccBytes = 128 * 1024;  // G x T accumulators
-constexpr int kEntCap = 4096;                // query entries staged in shared memory (32 KB)
+constexpr int kEntCap = 2048;                // query entries staged in shared memory (16 KB)
 constexpr int kItemCap = 9216;               // (term, 128-posting chunk) items per term batch (18 KB)
+constexpr int kTinySeg = 64;                 // segments shorter than this are packed, not itemised
+constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting chunks per term batch
 constexpr int kMaxGroup = 256;               // queries per group (thresholds kept in shared memory)
 constexpr int kHeadG = 32;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 32;
@@ -53,7 +55,7 @@ struct DtConfig {
 gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts, DtConfig* c) {
   if (!ix->seg) return GS_ERR_UNSUPPORTED;
   c->T = (opts && opts->tile_docs > 0) ? opts->tile_docs : ix->tile_docs;
-  if (c->T % ix->tile_docs != 0) return GS_ERR_INVALID_ARG;
+  if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
   // the dense head keeps one accumulator register per query of the group
@@ -265,10 +267,12 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
   uint2* ent_s = reinterpret_cast<uint2*>(dyn_smem + (size_t)G * T * sizeof(AccT));
   uint16_t* item_term = reinterpret_cast<uint16_t*>(ent_s + kEntCap);
+  uint16_t* chunk_j0 = item_term + kItemCap;
   __shared__ const uint8_t* s_p0[kDtThreads];  // first block of the term's segment
   __shared__ int32_t s_off[kDtThreads];         // segment start within that block
   __shared__ int32_t s_len[kDtThreads];         // postings in the segment
   __shared__ int32_t s_item[kDtThreads + 1];
+  __shared__ int32_t s_tp[kDtThreads + 1];     // packed position of each short segment
   __shared__ int32_t s_e0[kDtThreads], s_e1[kDtThreads];
   __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
 
   for (int j0 = 0; j0 < nterm; j0 += tb) {
     const int j = j0 + threadIdx.x;
-    int items = 0;
+    int items = 0, tiny = 0;
     if (threadIdx.x < tb && j < nterm) {
       const int32_t t = ut[j];
       const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
@@ -328,21 +332,65 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       s_len[threadIdx.x] = (int32_t)(e - s);
       s_e0[threadIdx.x] = __ldg(up + j);
       s_e1[threadIdx.x] = __ldg(up + j + 1);
-      if (e > s) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
+      if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
+      else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
     }
-    int total;
+    int total, tiny_total;
     const int xi = block_excl_scan(items, warp_buf, &total);
-    if (threadIdx.x < tb) s_item[threadIdx.x] = xi;
+    const int xt = block_excl_scan(tiny, warp_buf, &tiny_total);
+    if (threadIdx.x < tb) {
+      s_item[threadIdx.x] = xi;
+      s_tp[threadIdx.x] = xt;
+    }
+    if (threadIdx.x == 0) s_tp[tb] = tiny_total;
     for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
+    // packed chunk c starts inside the short segment that holds posting 32 c
+    for (int c = (xt + 31) / 32; 32 * c < xt + tiny; ++c) chunk_j0[c] = (uint16_t)threadIdx.x;
+    const int packed = (tiny_total + 31) / 32;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
+    const int units = total + packed;
     int nxt = 0;
     if (lane == 0) nxt = atomicAdd(&s_next, 1);
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    while (nxt < total) {
+    while (nxt < units) {
       const int it = nxt;
       if (lane == 0) nxt = atomicAdd(&s_next, 1);
       nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      if (it >= total) {
+        // 32 postings of the packed short segments: one posting per lane, its
+        // own term and entries
+        const int P = (it - total) * 32 + lane;
+        if (P < tiny_total) {
+          int jj = chunk_j0[it - total];
+          while (P >= s_tp[jj + 1]) ++jj;
+          const int rel = P - s_tp[jj] + s_off[jj];
+          const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
+          const int li = rel & 31;
+          const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
+          const uint32_t da = (uint32_t)(doc - doc0) * 4u;
+          AccT xv;
+          if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
+          else xv = (AccT)load_x<IMPACT>(blk, li);
+          const int32_t eb = s_e0[jj], ee = s_e1[jj];
+          for (int32_t en = eb; en < ee; ++en) {
+            uint2 E;
+            if (staged) {
+              E = ent_s[en - ent_lo];
+            } else {
+              E = __ldg(ent + en);
+              E.x *= row_bytes;
+            }
+            const uint32_t addr = acc_s + E.x + da;
+            if (IMPACT == GS_IMPACT_U8)
+              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)E.y * (int32_t)xv) : "memory");
+            else
+              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(E.y) * (float)xv)
+                           : "memory");
+          }
+        }
+        continue;
+      }
       const int jj = item_term[it];
       const int c = it - s_item[jj];
       const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
@@ -390,9 +438,11 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   }
 
   if (HEAD) {
-    // dense head: S[q][d] += sum_h W[q][h] * X[h][d] with one accumulator
-    // register per query (thread = document), weights broadcast from shared
-    // memory; every (query, document) cell is owned by one thread
+    // dense head: S[q][d] += sum_h W[q][h] * X[h][d], a register-blocked
+    // product.  Lane l of warp w owns queries 4 (l % 8) .. + 3 and documents
+    // 8 (4 w + l / 8) .. + 7 of each 1024-document slab: the 8 lanes that
+    // share documents read the same head bytes (one request), the 4 lanes
+    // groups that share queries read the same weights (broadcast).
     __shared__ __align__(16) AccT s_w[GS_MAX_HEAD_TERMS * kHeadG];
     __shared__ int32_t s_hact[GS_MAX_HEAD_TERMS];
     const int nact = head_nact[g];
@@ -403,34 +453,77 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       memcpy(&s_w[i], &raw, 4);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < T; d += blockDim.x) {
-      AccT r[kHeadG];
+    const int qb = lane & 7;
+    const int dbk = warp * 4 + (lane >> 3);  // 8-document block within the slab
+    for (int slab = 0; slab < T; slab += 1024) {
+      if (slab + dbk * 8 >= T) break;  // tiles shorter than 1024 documents
+      const int64_t col = doc0 + slab + dbk * 8;
+      AccT r[4][8];
 #pragma unroll
-      for (int q = 0; q < kHeadG; ++q) r[q] = (AccT)0;
-      const int64_t col = doc0 + d;
-      for (int a = 0; a < nact; ++a) {
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jd = 0; jd < 8; ++jd) r[i][jd] = (AccT)0;
+      auto load8 = [&](int a, AccT (&xo)[8]) {
         const int64_t at = (int64_t)s_hact[a] * head_ld + col;
-        AccT x;
-        if (IMPACT == GS_IMPACT_F32) x = __ldg(reinterpret_cast<const float*>(head_dense) + at);
-        else if (IMPACT == GS_IMPACT_F16) x = __half2float(__ldg(reinterpret_cast<const __half*>(head_dense) + at));
-        else if (IMPACT == GS_IMPACT_BF16)
-          x = __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(head_dense) + at));
-        else x = (AccT)__ldg(head_dense + at);
-        const AccT* wr = s_w + a * kHeadG;
+        if (IMPACT == GS_IMPACT_F32) {
+          const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(head_dense) + at);
+          const float4 u0 = __ldg(p), u1 = __ldg(p + 1);
+          xo[0] = u0.x; xo[1] = u0.y; xo[2] = u0.z; xo[3] = u0.w;
+          xo[4] = u1.x; xo[5] = u1.y; xo[6] = u1.z; xo[7] = u1.w;
+        } else if (IMPACT == GS_IMPACT_U8) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2*>(head_dense + at));
 #pragma unroll
-        for (int q4 = 0; q4 < kHeadG / 4; ++q4) {
-          AccT w4[4];
-          *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+          for (int jd = 0; jd < 4; ++jd) {
+            xo[jd] = (AccT)((u.x >> (8 * jd)) & 0xffu);
+            xo[4 + jd] = (AccT)((u.y >> (8 * jd)) & 0xffu);
+          }
+        } else {
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(head_dense + at * 2));
+          const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (IMPACT == GS_IMPACT_U8) r[4 * q4 + u] += w4[u] * x;
-            else r[4 * q4 + u] = fmaf((float)w4[u], (float)x, (float)r[4 * q4 + u]);
+          for (int jd = 0; jd < 4; ++jd) {
+            float2 f;
+            if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&w4[jd]));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[jd]));
+            xo[2 * jd] = (AccT)f.x;
+            xo[2 * jd + 1] = (AccT)f.y;
           }
         }
+      };
+      AccT xn[8];
+      if (nact > 0) load8(0, xn);
+      for (int a = 0; a < nact; ++a) {
+        AccT xc[8];
+#pragma unroll
+        for (int jd = 0; jd < 8; ++jd) xc[jd] = xn[jd];
+        if (a + 1 < nact) load8(a + 1, xn);  // next row in flight
+        AccT w4[4];
+        *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(s_w + a * kHeadG + 4 * qb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jd = 0; jd < 8; ++jd) {
+            if (IMPACT == GS_IMPACT_U8) r[i][jd] += w4[i] * xc[jd];
+            else r[i][jd] = fmaf((float)w4[i], (float)xc[jd], (float)r[i][jd]);
+          }
       }
 #pragma unroll
-      for (int q = 0; q < kHeadG; ++q)
-        if (q < gq) acc[q * T + d] += r[q];
+      for (int i = 0; i < 4; ++i) {
+        const int q = 4 * qb + i;
+        if (q < gq) {
+          AccT* dst = acc + q * T + slab + dbk * 8;
+          uint4 c0 = *reinterpret_cast<uint4*>(dst), c1 = *reinterpret_cast<uint4*>(dst + 4);
+          AccT* v0 = reinterpret_cast<AccT*>(&c0);
+          AccT* v1 = reinterpret_cast<AccT*>(&c1);
+#pragma unroll
+          for (int jd = 0; jd < 4; ++jd) {
+            v0[jd] += r[i][jd];
+            v1[jd] += r[i][4 + jd];
+          }
+          *reinterpret_cast<uint4*>(dst) = c0;
+          *reinterpret_cast<uint4*>(dst + 4) = c1;
+        }
+      }
     }
     __syncthreads();
   }
@@ -677,7 +770,8 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
 template <int IMPACT, bool HEAD>
 gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
                          const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
-  const size_t smem = (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + kItemCap * sizeof(uint16_t);
+  const size_t smem =
+      (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
   auto ks = dt_tile_kernel<IMPACT, kModeSample, HEAD>;
   auto km = dt_tile_kernel<IMPACT, kModeMain, HEAD>;
   GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
