@@ -277,6 +277,8 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
   __shared__ int s_next;
+  __shared__ __align__(16) AccT s_w[HEAD ? GS_MAX_HEAD_TERMS * kHeadG : 4];
+  __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
   const int g = blockIdx.x % ng;
   const int tile_idx = blockIdx.x / ng;
@@ -315,6 +317,25 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
       ent_s[i] = make_uint2(E.x * row_bytes, E.y);
     }
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  int nact = 0;
+  if (HEAD) {
+    // head rows and weights of the group; the tile's head rows are prefetched
+    // into L2 now so that they are resident when the head phase reads them
+    nact = head_nact[g];
+    for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
+      const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
+      memcpy(&s_w[i], &raw, 4);
+    }
+    const int ib = impact_bytes(IMPACT);
+    const int lines_per_row = (T * ib + 127) / 128;
+    for (int i = threadIdx.x; i < nact * lines_per_row; i += blockDim.x) {
+      const uint8_t* ptr = head_dense + ((int64_t)s_hact[i / lines_per_row] * head_ld + doc0) * ib +
+                           (int64_t)(i % lines_per_row) * 128;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+    }
+  }
   // terms per batch: their 128-posting work items must fit the item table
   const int items_per_term = T / 128 + 1;
   const int tb = min(kDtThreads, kItemCap / items_per_term);
@@ -438,90 +459,76 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
   }
 
   if (HEAD) {
-    // dense head: S[q][d] += sum_h W[q][h] * X[h][d], a register-blocked
-    // product.  Lane l of warp w owns queries 4 (l % 8) .. + 3 and documents
-    // 8 (4 w + l / 8) .. + 7 of each 1024-document slab: the 8 lanes that
-    // share documents read the same head bytes (one request), the 4 lanes
-    // groups that share queries read the same weights (broadcast).
-    __shared__ __align__(16) AccT s_w[GS_MAX_HEAD_TERMS * kHeadG];
-    __shared__ int32_t s_hact[GS_MAX_HEAD_TERMS];
-    const int nact = head_nact[g];
-    for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
-      const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
-      memcpy(&s_w[i], &raw, 4);
-    }
-    __syncthreads();
-    const int qb = lane & 7;
-    const int dbk = warp * 4 + (lane >> 3);  // 8-document block within the slab
+    // dense head: S[q][d] += sum_h W[q][h] * X[h][d].  Thread (warp w, lane
+    // l) owns queries 16 (w % 2) .. + 15 and documents 2 p, 2 p + 1 of each
+    // 1024-document slab, p = 32 (w / 2) + l: the head rows are read
+    // coalesced, four rows in flight, the weights are warp-wide broadcasts,
+    // and every (query, document) cell has one owner (no atomics).
+    const int qh = warp & 1;
+    const int dp = (warp >> 1) * 32 + lane;
     for (int slab = 0; slab < T; slab += 1024) {
-      if (slab + dbk * 8 >= T) break;  // tiles shorter than 1024 documents
-      const int64_t col = doc0 + slab + dbk * 8;
-      AccT r[4][8];
+      if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
+      const int64_t col = doc0 + slab + 2 * dp;
+      AccT r[16][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jd = 0; jd < 8; ++jd) r[i][jd] = (AccT)0;
-      auto load8 = [&](int a, AccT (&xo)[8]) {
+      for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
+      auto load2 = [&](int a, AccT& x0, AccT& x1) {
         const int64_t at = (int64_t)s_hact[a] * head_ld + col;
         if (IMPACT == GS_IMPACT_F32) {
-          const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(head_dense) + at);
-          const float4 u0 = __ldg(p), u1 = __ldg(p + 1);
-          xo[0] = u0.x; xo[1] = u0.y; xo[2] = u0.z; xo[3] = u0.w;
-          xo[4] = u1.x; xo[5] = u1.y; xo[6] = u1.z; xo[7] = u1.w;
+          const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
+          x0 = u.x;
+          x1 = u.y;
         } else if (IMPACT == GS_IMPACT_U8) {
-          const uint2 u = __ldg(reinterpret_cast<const uint2*>(head_dense + at));
-#pragma unroll
-          for (int jd = 0; jd < 4; ++jd) {
-            xo[jd] = (AccT)((u.x >> (8 * jd)) & 0xffu);
-            xo[4 + jd] = (AccT)((u.y >> (8 * jd)) & 0xffu);
-          }
+          const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
+          x0 = (AccT)(u & 0xffu);
+          x1 = (AccT)(u >> 8);
         } else {
-          const uint4 u = __ldg(reinterpret_cast<const uint4*>(head_dense + at * 2));
-          const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-          for (int jd = 0; jd < 4; ++jd) {
-            float2 f;
-            if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&w4[jd]));
-            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[jd]));
-            xo[2 * jd] = (AccT)f.x;
-            xo[2 * jd + 1] = (AccT)f.y;
-          }
+          const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
+          float2 f;
+          if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+          else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+          x0 = (AccT)f.x;
+          x1 = (AccT)f.y;
         }
       };
-      AccT xn[8];
-      if (nact > 0) load8(0, xn);
-      for (int a = 0; a < nact; ++a) {
-        AccT xc[8];
+      for (int a0 = 0; a0 < nact; a0 += 4) {
+        AccT xs[4][2];
 #pragma unroll
-        for (int jd = 0; jd < 8; ++jd) xc[jd] = xn[jd];
-        if (a + 1 < nact) load8(a + 1, xn);  // next row in flight
-        AccT w4[4];
-        *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(s_w + a * kHeadG + 4 * qb);
+        for (int u = 0; u < 4; ++u) {
+          xs[u][0] = xs[u][1] = (AccT)0;
+          if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+        }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int u = 0; u < 4; ++u) {
+          if (a0 + u >= nact) break;
+          const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
 #pragma unroll
-          for (int jd = 0; jd < 8; ++jd) {
-            if (IMPACT == GS_IMPACT_U8) r[i][jd] += w4[i] * xc[jd];
-            else r[i][jd] = fmaf((float)w4[i], (float)xc[jd], (float)r[i][jd]);
+          for (int q4 = 0; q4 < 4; ++q4) {
+            AccT w4[4];
+            *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              if (IMPACT == GS_IMPACT_U8) {
+                r[4 * q4 + v][0] += w4[v] * xs[u][0];
+                r[4 * q4 + v][1] += w4[v] * xs[u][1];
+              } else {
+                r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
+                r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+              }
+            }
           }
+        }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int q = 4 * qb + i;
+      for (int i = 0; i < 16; ++i) {
+        const int q = 16 * qh + i;
         if (q < gq) {
-          AccT* dst = acc + q * T + slab + dbk * 8;
-          uint4 c0 = *reinterpret_cast<uint4*>(dst), c1 = *reinterpret_cast<uint4*>(dst + 4);
-          AccT* v0 = reinterpret_cast<AccT*>(&c0);
-          AccT* v1 = reinterpret_cast<AccT*>(&c1);
-#pragma unroll
-          for (int jd = 0; jd < 4; ++jd) {
-            v0[jd] += r[i][jd];
-            v1[jd] += r[i][4 + jd];
-          }
-          *reinterpret_cast<uint4*>(dst) = c0;
-          *reinterpret_cast<uint4*>(dst + 4) = c1;
+          AccT* dst = acc + q * T + slab + 2 * dp;
+          uint2 c = *reinterpret_cast<uint2*>(dst);
+          AccT* v = reinterpret_cast<AccT*>(&c);
+          v[0] += r[i][0];
+          v[1] += r[i][1];
+          *reinterpret_cast<uint2*>(dst) = c;
         }
       }
     }
