@@ -59,7 +59,11 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
   // the dense head keeps one accumulator register per query of the group
-  const bool head = ix->head_H > 0 && !(opts && opts->use_head < 0) && G == kHeadG;
+  // auto: the head pays off where shared-memory float reductions are slow;
+  // integer reductions (uint8 path) are cheap enough without it
+  const int use_head = opts ? opts->use_head : 0;
+  const bool head = ix->head_H > 0 && G == kHeadG &&
+                    (use_head > 0 || (use_head == 0 && ix->impact != GS_IMPACT_U8));
   c->H = head ? ix->head_H : 0;
   G = head ? kHeadG : std::min(std::min(G, B), kMaxGroup);
   if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {

@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 ALGOS = ["term_parallel", "doc_tiled"]
 # the doc-tiled kernel with and without the dense head
-VARIANTS = [("term_parallel", {}), ("doc_tiled", {}), ("doc_tiled", {"use_head": -1})]
+VARIANTS = [("term_parallel", {}), ("doc_tiled", {}), ("doc_tiled", {"use_head": -1}),
+            ("doc_tiled", {"use_head": 1})]
 
 
 def _gs():
