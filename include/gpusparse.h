@@ -264,6 +264,36 @@ gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, in
  * call that used `workspace` raised. */
 gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags);
 
+/* --- search without allocation (the paper has no counterpart) ------------
+ *
+ * Some callers cannot call cudaMalloc: code that runs where another
+ * allocator owns all of the device's memory (a host framework's fixed pool,
+ * a memory-capped sandbox), and latency-critical request paths where
+ * cudaMalloc / cudaFree would synchronise the device.  gs_search_static
+ * serves them: it is gs_search with its scratch taken from one file-scope
+ * array of device memory of GS_STATIC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.  The caller still
+ * passes the queries and the output arrays (device memory, as for
+ * gs_search).
+ *   - Batches whose workspace (gs_search_workspace_size) exceeds
+ *     GS_STATIC_SCRATCH_BYTES are rejected with GS_ERR_WORKSPACE; nothing is
+ *     allocated then either.
+ *   - The first call on a device looks the array's device address up with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the search clears what it needs itself.  Calls that overlap on
+ *     the GPU (other streams, other host threads) race on the array: serialise
+ *     them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - gs_search_flags() takes the workspace pointer and therefore does not
+ *     apply; data errors still skip the offending query terms. */
+#define GS_STATIC_SCRATCH_BYTES (64u << 20)
+
+gs_status gs_search_static(const gs_index* index, const int32_t* q_indptr, const int32_t* q_terms,
+                           const float* q_w, int32_t batch, int64_t q_nnz, int32_t k, int32_t* out_ids,
+                           void* out_scores, const gs_search_opts* opts, gs_stream_t stream);
+
 /* --- misc ---------------------------------------------------------------- */
 
 const char* gs_status_str(gs_status status);

@@ -23,11 +23,12 @@ ALGOS = {"auto": 0, "term_parallel": 1, "doc_tiled": 2, "doc_parallel": 3}
 GS_FLAG_BAD_TERM, GS_FLAG_BAD_WEIGHT, GS_FLAG_CAND_OVERFLOW = 1, 2, 4
 GS_FLAG_TIMEOUT, GS_FLAG_BAD_INDPTR = 8, 16
 GS_MAX_K = 2048
+GS_STATIC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
-    "gs_search_plan",
+    "gs_search_plan", "gs_search_static",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
 )
 GS_NUM_STAGE_EVENTS = 6
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
     L.gs_score_dense.restype = ctypes.c_int
     L.gs_search_plan.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), ctypes.POINTER(gs_plan_info)]
     L.gs_search_plan.restype = ctypes.c_int
+    L.gs_search_static.argtypes = [P, P, P, P, I32, I64, I32, P, P, ctypes.POINTER(gs_search_opts), P]
+    L.gs_search_static.restype = ctypes.c_int
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -275,6 +278,21 @@ def gs_search(index: Index, q: Queries, k: int, opts=None, workspace=None, out_i
     _check(L.gs_search(index.handle, _ptr(q.indptr), _ptr(q.terms), _ptr(q.weights), B, q.nnz, k, _ptr(out_ids),
                        _ptr(out_scores), _ptr(workspace), workspace.numel(), ctypes.byref(opts) if opts else None,
                        _stream(stream)), "gs_search")
+    return out_ids, out_scores
+
+
+def gs_search_static(index: Index, q: Queries, k: int, opts=None, out_ids=None, out_scores=None, stream=None):
+    """gs_search with the library's fixed scratch array instead of a workspace (no allocation inside)."""
+    L = load()
+    B = q.batch
+    dev = q.indptr.device
+    if out_ids is None:
+        out_ids = torch.empty((B, k), dtype=torch.int32, device=dev)
+    if out_scores is None:
+        out_scores = torch.empty((B, k), dtype=index.score_dtype, device=dev)
+    _check(L.gs_search_static(index.handle, _ptr(q.indptr), _ptr(q.terms), _ptr(q.weights), B, q.nnz, k,
+                              _ptr(out_ids), _ptr(out_scores), ctypes.byref(opts) if opts else None,
+                              _stream(stream)), "gs_search_static")
     return out_ids, out_scores
 
 
