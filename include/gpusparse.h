@@ -100,7 +100,7 @@ typedef enum {
                                    the row was recomputed on the dense path */
 #define GS_FLAG_TIMEOUT 8u      /* a bounded device wait gave up */
 #define GS_FLAG_BAD_INDPTR 16u  /* the query CSR row pointer was not monotone
-                                   or did not end at q_nnz: results undefined */
+                                   or ended past q_nnz: results undefined */
 
 typedef struct gs_index gs_index;
 
@@ -210,8 +210,10 @@ gs_status gs_search_workspace_size(const gs_index* index, int32_t batch, int64_t
 /* Exact top-k of a batch of queries (Sec. 4, Eq. 4-5 + exact top-k).
  * Queries are CSR on the device:
  *   q_indptr [batch + 1] int32, q_indptr[0] = 0, non-decreasing,
- *             q_indptr[batch] = q_nnz;
+ *             q_indptr[batch] <= q_nnz;
  *   q_terms  [q_nnz] int32 term ids; q_w [q_nnz] float32 weights.
+ *   q_nnz is the capacity of q_terms / q_w: entries past q_indptr[batch]
+ *   are ignored (a captured graph can serve batches of fewer terms).
  *   A term may repeat inside a query: every occurrence contributes.
  * Outputs on the device, row-major [batch x k]:
  *   out_ids    int32 document ids, ordered by (score desc, id asc);
@@ -263,6 +265,30 @@ gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, in
 /* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits the last
  * call that used `workspace` raised. */
 gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags);
+
+/* --- uneven batches from captured CUDA graphs -----------------------------
+ *
+ * A runner owns device buffers for up to max_batch queries / max_q_nnz query
+ * terms / max_k results, a workspace and one CUDA graph per (batch bucket, k):
+ * batches are padded to a power-of-two bucket with empty queries.  The first
+ * batch of a bucket is used to time candidate doc-tiled plans (tile length,
+ * queries per group, sample stride, dense head; autotune != 0) — the
+ * grid-search analogue of the paper's BLOCK_PL tuning (Sec. 5.2) — and the
+ * chosen plan's gs_search is captured into a graph that later batches replay
+ * with one launch.  Queries and results are in host memory; the call
+ * synchronises `stream`.  gs_runner_create allocates (device and pinned host
+ * memory); gs_runner_search does not.  A runner serialises its own calls. */
+typedef struct gs_runner gs_runner;
+
+gs_status gs_runner_create(const gs_index* index, int32_t max_batch, int64_t max_q_nnz, int32_t max_k,
+                           const gs_search_opts* opts, int32_t autotune, gs_runner** out);
+gs_status gs_runner_search(gs_runner* runner, const int32_t* h_q_indptr, const int32_t* h_q_terms,
+                           const float* h_q_w, int32_t batch, int32_t k, int32_t* h_out_ids,
+                           void* h_out_scores, gs_stream_t stream);
+/* the plan a bucket runs with (after its first batch), and its tuned time */
+gs_status gs_runner_plan(gs_runner* runner, int32_t batch, int32_t k, gs_search_opts* out_opts,
+                         float* out_tuned_ms);
+void gs_runner_free(gs_runner* runner);
 
 /* --- search without allocation (the paper has no counterpart) ------------
  *

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "gs_doctiled.cuh"
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
   for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     if (q_indptr[q + 1] < q_indptr[q]) fl |= GS_FLAG_BAD_INDPTR;
   }
-  if (threadIdx.x == 0 && (q_indptr[0] != 0 || q_indptr[B] != q_nnz)) fl |= GS_FLAG_BAD_INDPTR;
+  if (threadIdx.x == 0 && (q_indptr[0] != 0 || q_indptr[B] > q_nnz || q_indptr[B] < 0)) fl |= GS_FLAG_BAD_INDPTR;
   const int32_t e0 = min(max(q_indptr[q0], 0), q_nnz);
   const int32_t e1 = min(max(q_indptr[q1], e0), q_nnz);
   uint32_t* cnt = cnt_all + (int64_t)g * V;
@@ -785,8 +786,22 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
       (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
   auto ks = dt_tile_kernel<IMPACT, kModeSample, HEAD>;
   auto km = dt_tile_kernel<IMPACT, kModeMain, HEAD>;
-  GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  GS_CUDA_TRY(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the dynamic shared-memory ceiling only grows, once per device: no
+  // attribute call is issued while a stream is being captured for a graph
+  static std::mutex mu;
+  static size_t set_for[128] = {};
+  {
+    int dev = 0;
+    GS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 128) return GS_ERR_UNSUPPORTED;
+    if (set_for[dev] < smem) {
+      const size_t ceil_bytes = (size_t)kDtMaxAccBytes + kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
+      GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ceil_bytes));
+      GS_CUDA_TRY(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ceil_bytes));
+      set_for[dev] = ceil_bytes;
+    }
+  }
   if (c.R > 0) {
     ks<<<c.n_sample * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N,
                                                    q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample,

@@ -66,13 +66,20 @@ __global__ void __launch_bounds__(kPrepThreads) tp_prep_kernel(
   for (int q = threadIdx.x; q < B; q += blockDim.x) {
     if (q_indptr[q + 1] < q_indptr[q]) flags |= GS_FLAG_BAD_INDPTR;
   }
-  if (threadIdx.x == 0 && (q_indptr[0] != 0 || (int64_t)q_indptr[B] != q_nnz)) flags |= GS_FLAG_BAD_INDPTR;
+  if (threadIdx.x == 0 && (q_indptr[0] != 0 || (int64_t)q_indptr[B] > q_nnz || q_indptr[B] < 0))
+    flags |= GS_FLAG_BAD_INDPTR;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // entries past q_indptr[B] are unused capacity
+  const int64_t n_used = min((int64_t)max(q_indptr[B], 0), q_nnz);
   for (int64_t base = 0; base < q_nnz; base += blockDim.x) {
     const int64_t p = base + threadIdx.x;
     int64_t nch = 0;
     if (p < q_nnz) {
+      pair_q[p] = 0;
+      pair_t[p] = 0;
+    }
+    if (p < n_used) {
       const int q = upper_bound_i32(q_indptr, B + 1, (int32_t)p) - 1;
       const int32_t t = q_terms[p];
       const float w = q_w[p];

@@ -28,7 +28,8 @@ GS_STATIC_SCRATCH_BYTES = 64 << 20
 EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
-    "gs_search_plan", "gs_search_static",
+    "gs_search_plan", "gs_search_static", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
+    "gs_runner_free",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
 )
 GS_NUM_STAGE_EVENTS = 6
@@ -113,6 +114,14 @@ def load(path: str = LIB_PATH):
     L.gs_search_plan.restype = ctypes.c_int
     L.gs_search_static.argtypes = [P, P, P, P, I32, I64, I32, P, P, ctypes.POINTER(gs_search_opts), P]
     L.gs_search_static.restype = ctypes.c_int
+    L.gs_runner_create.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), I32, ctypes.POINTER(P)]
+    L.gs_runner_create.restype = ctypes.c_int
+    L.gs_runner_search.argtypes = [P, P, P, P, I32, I32, P, P, P]
+    L.gs_runner_search.restype = ctypes.c_int
+    L.gs_runner_plan.argtypes = [P, I32, I32, ctypes.POINTER(gs_search_opts), ctypes.POINTER(ctypes.c_float)]
+    L.gs_runner_plan.restype = ctypes.c_int
+    L.gs_runner_free.argtypes = [P]
+    L.gs_runner_free.restype = None
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -327,6 +336,50 @@ def gs_search_flags(workspace: torch.Tensor, stream=None) -> int:
     f = ctypes.c_uint32(0)
     _check(L.gs_search_flags(_ptr(workspace), _stream(stream), ctypes.byref(f)), "gs_search_flags")
     return int(f.value)
+
+
+class Runner:
+    """Uneven batches from captured CUDA graphs, tile shapes autotuned per batch bucket (gs_runner_*)."""
+
+    def __init__(self, index: Index, max_batch: int, max_q_nnz: int, max_k: int, opts=None, autotune=True):
+        self._L = load()
+        self.index = index  # keeps the index alive
+        h = ctypes.c_void_p()
+        _check(self._L.gs_runner_create(index.handle, max_batch, max_q_nnz, max_k,
+                                        ctypes.byref(opts) if opts else None, 1 if autotune else 0,
+                                        ctypes.byref(h)), "gs_runner_create")
+        self._h = h
+        self.max_batch, self.max_k = max_batch, max_k
+
+    def search(self, h_indptr, h_terms, h_w, k: int, out_ids=None, out_scores=None, stream=None):
+        """Host tensors in (int32 indptr/terms, float32 weights), host tensors out; synchronous."""
+        B = h_indptr.numel() - 1
+        if out_ids is None:
+            out_ids = torch.empty((B, k), dtype=torch.int32)
+        if out_scores is None:
+            out_scores = torch.empty((B, k), dtype=self.index.score_dtype)
+        _check(self._L.gs_runner_search(self._h, _ptr(h_indptr), _ptr(h_terms), _ptr(h_w), B, k, _ptr(out_ids),
+                                        _ptr(out_scores), _stream(stream)), "gs_runner_search")
+        return out_ids, out_scores
+
+    def plan(self, batch: int, k: int):
+        o = gs_search_opts()
+        ms = ctypes.c_float(0)
+        _check(self._L.gs_runner_plan(self._h, batch, k, ctypes.byref(o), ctypes.byref(ms)), "gs_runner_plan")
+        return {"algo": o.algo, "tile_docs": o.tile_docs, "group_queries": o.group_queries,
+                "sample_stride": o.sample_stride, "use_head": o.use_head, "chunk_blocks": o.chunk_blocks,
+                "tuned_ms": ms.value}
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self._L.gs_runner_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def gs_version() -> int:

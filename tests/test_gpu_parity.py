@@ -302,3 +302,28 @@ def test_medium_workload_1m():
         for algo, kw in VARIANTS:
             c.check(1000, algo, **kw)
         c.idx.free()
+
+
+def test_runner_graph_replay_matches_search():
+    """Uneven batches through captured graphs (autotuned plans) equal the direct search."""
+    gs = _gs()
+    docs = synth.docs(60_000, seed=6)
+    qs = synth.queries(40, seed=6, law=synth.MIXTURE_LAW)
+    for impact in ("u8", "f32"):
+        c = Case(docs, qs, impact, tile_docs=1024)
+        runner = gs.Runner(c.idx, max_batch=32, max_q_nnz=int(qs.nnz), max_k=100)
+        for (lo, hi) in [(0, 1), (1, 6), (6, 38), (0, 3), (3, 6)]:
+            sub = qs.slice(lo, hi)
+            for k in (10, 100):
+                for _rep in range(2):  # first call tunes and captures, second replays
+                    ids, sc = runner.search(torch.from_numpy(sub.indptr.astype(np.int32)),
+                                            torch.from_numpy(sub.terms), torch.from_numpy(sub.weights), k)
+                    rid, rsc, _ = c.ref.topk(sub.indptr, sub.terms, sub.weights, k)
+                    if impact == "u8":
+                        check.check_u8(ids.numpy(), sc.numpy(), rid, rsc)
+                    else:
+                        check.check_float(c.ref, sub.indptr, sub.terms, sub.weights, ids.numpy(), sc.numpy(), rid,
+                                          rsc, docs.n)
+        plan = runner.plan(8, 10)
+        assert plan["tile_docs"] % 1024 == 0 and plan["tuned_ms"] > 0
+        runner.free()
