@@ -275,8 +275,9 @@ gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* f
  * queries per group, sample stride, dense head; autotune != 0) — the
  * grid-search analogue of the paper's BLOCK_PL tuning (Sec. 5.2) — and the
  * chosen plan's gs_search is captured into a graph that later batches replay
- * with one launch.  Queries and results are in host memory; the call
- * synchronises `stream`.  gs_runner_create allocates (device and pinned host
+ * with one launch.  Queries and results are in host memory; the work runs
+ * on the runner's own stream after the work already queued on `stream`, and
+ * the call returns when the results are in host memory.  gs_runner_create allocates (device and pinned host
  * memory); gs_runner_search does not.  A runner serialises its own calls. */
 typedef struct gs_runner gs_runner;
 

@@ -37,6 +37,10 @@ struct gs_runner {
   int32_t* h_indptr = nullptr;
   int32_t* h_terms = nullptr;
   float* h_w = nullptr;
+  // graphs are captured and replayed on the runner's own stream: capture is
+  // not possible on the legacy default stream a caller may pass
+  cudaStream_t own = nullptr;
+  cudaEvent_t dep = nullptr;
   struct Entry {
     gs_search_opts opts{};
     cudaGraph_t graph = nullptr;
@@ -168,6 +172,8 @@ void free_runner(gs_runner* r) {
   cudaFreeHost(r->h_indptr);
   cudaFreeHost(r->h_terms);
   cudaFreeHost(r->h_w);
+  if (r->dep) cudaEventDestroy(r->dep);
+  if (r->own) cudaStreamDestroy(r->own);
   delete r;
 }
 
@@ -209,7 +215,9 @@ extern "C" gs_status gs_runner_create(const gs_index* index, int32_t max_batch, 
       (e = cudaMalloc(&r->ws, need)) != cudaSuccess ||
       (e = cudaMallocHost(&r->h_indptr, sizeof(int32_t) * (B1 + 1))) != cudaSuccess ||
       (e = cudaMallocHost(&r->h_terms, sizeof(int32_t) * max_q_nnz)) != cudaSuccess ||
-      (e = cudaMallocHost(&r->h_w, sizeof(float) * max_q_nnz)) != cudaSuccess) {
+      (e = cudaMallocHost(&r->h_w, sizeof(float) * max_q_nnz)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&r->own, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&r->dep, cudaEventDisableTiming)) != cudaSuccess) {
     gs::set_cuda_error(e);
     free_runner(r);
     return e == cudaErrorMemoryAllocation ? GS_ERR_OUT_OF_MEMORY : GS_ERR_CUDA;
@@ -231,7 +239,10 @@ extern "C" gs_status gs_runner_search(gs_runner* r, const int32_t* h_q_indptr, c
   for (int32_t q = 0; q < batch; ++q)
     if (h_q_indptr[q + 1] < h_q_indptr[q]) return GS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(r->mu);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // work already queued on the caller's stream comes first
+  GS_CUDA_TRY(cudaEventRecord(r->dep, reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t s = r->own;
+  GS_CUDA_TRY(cudaStreamWaitEvent(s, r->dep, 0));
   const int bucket = pow2_at_least(batch);
   // padded batch: queries past `batch` are empty
   std::memcpy(r->h_indptr, h_q_indptr, sizeof(int32_t) * (batch + 1));
