@@ -427,6 +427,93 @@ def run_uneven(args, w):
             "steps_per_point": steps, "results": results}
 
 
+def run_serving(args, w):
+    """Poisson arrivals over two resident FP16 indexes (1M and 8.84M docs), continuous batching."""
+    import threading
+    import torch
+    from paper_2606_26441_gb300 import gpusparse as gs
+    gs.load()
+    dev = torch.device("cuda:0")
+    big = synth.docs(synth.N_8_8M, seed=0, threads=cores())
+    small = synth.docs(1_000_000, seed=1, threads=cores())
+    idx = []
+    for d in (small, big):
+        idx.append(gs.gs_index_build(torch.from_numpy(d.indptr).to(dev), torch.from_numpy(d.terms).to(dev),
+                                     torch.from_numpy(d.weights).to(dev), d.vocab, "f16"))
+    # the plain FP32 batch-500 form on the 8.84M collection, same GPU, same run
+    f32 = gs.gs_index_build(torch.from_numpy(big.indptr).to(dev), torch.from_numpy(big.terms).to(dev),
+                            torch.from_numpy(big.weights).to(dev), big.vocab, "f32")
+    qb = synth.queries(500, seed=5)
+    q = gs.Queries.from_numpy(qb.indptr, qb.terms, qb.weights, dev)
+    o = gs.make_opts("term_parallel")
+    ws = gs.alloc_workspace(f32, 500, q.nnz, 1000, o)
+    ts = []
+    for i in range(4):
+        t0 = time.perf_counter()
+        gs.gs_search(f32, q, 1000, o, ws)
+        torch.cuda.synchronize()
+        if i:
+            ts.append((time.perf_counter() - t0) * 1e3)
+    plain = {"form": "term-parallel FP32, batch 500, 8.84M docs, k=1000", "batch_ms": float(np.median(ts)),
+             "qps": 500 / (np.median(ts) / 1e3)}
+    del ws, f32
+    torch.cuda.empty_cache()
+    server = gs.Server(idx, lanes=4, max_batch=256, max_q_nnz=256 * 64, max_k=1000, max_wait_us=500)
+    rng = np.random.default_rng(0)
+    qs = synth.queries(60_000, seed=9, law=w.query_law)
+    out = []
+    qi = 0
+    for rate in w.extra["rates"]:
+        n = int(min(rate * w.extra["seconds"], 20_000))
+        gaps = rng.exponential(1.0 / rate, n)
+        ks = rng.choice([10, 100, 1000], n)
+        which = rng.integers(0, 2, n)
+        rows = [qs.row((qi + i) % qs.n) for i in range(n)]
+        qi += n
+        rows = [(np.ascontiguousarray(t), np.ascontiguousarray(wt)) for t, wt in rows]
+        tickets = [None] * n
+        lat = np.zeros(n)
+        done = threading.Event()
+
+        def waiter():
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                lat[i] = server.wait(tickets[i], int(ks[i]), idx[which[i]].score_dtype, timeout_us=60_000_000)[2]
+            done.set()
+
+        th = threading.Thread(target=waiter)
+        st0 = server.stats()
+        th.start()
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n):
+            due += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 0.002:
+                    time.sleep(due - now - 0.001)
+            tickets[i] = server.submit(int(which[i]), rows[i][0], rows[i][1], int(ks[i]))
+        th.join()
+        elapsed = time.perf_counter() - t0
+        st1 = server.stats()
+        nb = st1["batches"] - st0["batches"]
+        out.append({"offered_qps": rate, "requests": n, "sustained_qps": n / elapsed,
+                    "p50_ms": float(np.percentile(lat, 50) / 1e3), "p99_ms": float(np.percentile(lat, 99) / 1e3),
+                    "batches": nb, "mean_batch": (st1["batched_queries"] - st0["batched_queries"]) / max(nb, 1)})
+        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    stats = server.stats()
+    server.close()
+    return {"suite": "serving", "metric": "per-request p50/p99 latency (submit to completion) and sustained QPS "
+            "under Poisson arrivals, continuous batching over two resident FP16 indexes",
+            "indexes": ["1M docs f16", "8.84M docs f16"], "k": "uniform over {10,100,1000}",
+            "query_nnz": "mixture law", "server": {"lanes": stats["lanes"], "max_batch": 256,
+                                                   "max_wait_us": 500, "max_in_flight": stats["max_in_flight"]},
+            "plain_fp32_batch500": plain, "results": out}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -434,6 +521,10 @@ def main():
     if w.extra.get("batches"):
         if rank == 0:
             print(json.dumps(run_uneven(args, w)), flush=True)
+        return
+    if w.extra.get("rates"):
+        if rank == 0:
+            print(json.dumps(run_serving(args, w)), flush=True)
         return
     t0 = time.perf_counter()
     docs = synth.docs(w.n_docs, seed=0, threads=cores())

@@ -291,6 +291,60 @@ gs_status gs_runner_plan(gs_runner* runner, int32_t batch, int32_t k, gs_search_
                          float* out_tuned_ms);
 void gs_runner_free(gs_runner* runner);
 
+/* --- serving loop with continuous batching --------------------------------
+ *
+ * (Sec. 7, future work 3: streaming query batching.)  Requests — one query,
+ * its k, the index it targets — are submitted from any host thread and
+ * queued.  A lane is one admission slot: a stream, a search workspace (the
+ * score memory of one batch), device and pinned buffers; the number of lanes
+ * follows from workspace_budget_bytes (when > 0) and `lanes`, so requests are
+ * admitted as score-buffer memory frees up.  A scheduler thread forms a batch
+ * from the oldest pending request's index whenever a lane is free (optionally
+ * waiting up to max_wait_us for more requests) and runs it on the lane's
+ * stream; batches of different lanes overlap on the GPU.  Each lane's
+ * completion thread hands every request the first k results of its batch
+ * (the batch runs with the largest k among its requests).  Several indexes
+ * may be resident at once.  Waits are bounded: gs_server_wait returns
+ * GS_ERR_TIMEOUT after timeout_us and the request can be waited for again. */
+typedef struct gs_server gs_server;
+
+typedef struct {
+  int32_t lanes;                  /* admission slots (batches in flight) */
+  int32_t max_batch;              /* queries per batch */
+  int32_t max_q_nnz;              /* query terms per batch */
+  int32_t max_k;                  /* largest k a request may ask for */
+  int32_t max_wait_us;            /* accumulation window once a lane is free (0 = none) */
+  int32_t reserved;
+  int64_t workspace_budget_bytes; /* > 0: lanes = min(lanes, budget / lane workspace) */
+  gs_search_opts opts;            /* search plan for every batch */
+} gs_server_config;
+
+typedef struct {
+  int32_t lanes;
+  int32_t max_in_flight;          /* most lanes busy at once */
+  int64_t completed;
+  int64_t batches;
+  int64_t batched_queries;        /* sum of batch sizes */
+  int64_t queued;                 /* requests waiting for a lane */
+  int64_t lane_workspace_bytes;
+} gs_server_stats;
+
+/* indexes: n_indexes resident indexes (owned by the caller, kept alive until
+ * gs_server_destroy); index ids in requests are positions in this array. */
+gs_status gs_server_create(const gs_index* const* indexes, int32_t n_indexes, const gs_server_config* cfg,
+                           gs_server** out);
+/* copies the query (host memory); *ticket identifies the request */
+gs_status gs_server_submit(gs_server* server, int32_t index_id, const int32_t* terms, const float* weights,
+                           int32_t nnz, int32_t k, int64_t* ticket);
+/* waits at most timeout_us for the request; on GS_OK writes k ids and k
+ * scores (float32, int32 on uint8 indexes) to host memory and, when
+ * latency_us is not NULL, the time from submit to completion */
+gs_status gs_server_wait(gs_server* server, int64_t ticket, int32_t* out_ids, void* out_scores, int64_t timeout_us,
+                         double* latency_us);
+gs_status gs_server_stats_get(gs_server* server, gs_server_stats* out);
+/* stops the threads after the batches in flight complete; queued requests are dropped */
+void gs_server_destroy(gs_server* server);
+
 /* --- search without allocation (the paper has no counterpart) ------------
  *
  * Some callers cannot call cudaMalloc: code that runs where another

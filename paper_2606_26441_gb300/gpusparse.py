@@ -29,7 +29,8 @@ EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
     "gs_search_plan", "gs_search_static", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
-    "gs_runner_free",
+    "gs_runner_free", "gs_server_create", "gs_server_submit", "gs_server_wait", "gs_server_stats_get",
+    "gs_server_destroy",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
 )
 GS_NUM_STAGE_EVENTS = 6
@@ -77,6 +78,18 @@ class gs_plan_info(ctypes.Structure):
                 ("reserved", ctypes.c_int64 * 3)]
 
 
+class gs_server_config(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_q_nnz", ctypes.c_int32),
+                ("max_k", ctypes.c_int32), ("max_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("workspace_budget_bytes", ctypes.c_int64), ("opts", gs_search_opts)]
+
+
+class gs_server_stats(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("batched_queries", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("lane_workspace_bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -122,6 +135,16 @@ def load(path: str = LIB_PATH):
     L.gs_runner_plan.restype = ctypes.c_int
     L.gs_runner_free.argtypes = [P]
     L.gs_runner_free.restype = None
+    L.gs_server_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(gs_server_config), ctypes.POINTER(P)]
+    L.gs_server_create.restype = ctypes.c_int
+    L.gs_server_submit.argtypes = [P, I32, P, P, I32, I32, ctypes.POINTER(I64)]
+    L.gs_server_submit.restype = ctypes.c_int
+    L.gs_server_wait.argtypes = [P, I64, P, P, I64, ctypes.POINTER(ctypes.c_double)]
+    L.gs_server_wait.restype = ctypes.c_int
+    L.gs_server_stats_get.argtypes = [P, ctypes.POINTER(gs_server_stats)]
+    L.gs_server_stats_get.restype = ctypes.c_int
+    L.gs_server_destroy.argtypes = [P]
+    L.gs_server_destroy.restype = None
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -378,6 +401,59 @@ class Runner:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving loop over resident indexes (gs_server_*)."""
+
+    def __init__(self, indexes, lanes=4, max_batch=256, max_q_nnz=16384, max_k=1000, max_wait_us=0,
+                 workspace_budget_bytes=0, opts=None):
+        self._L = load()
+        self.indexes = list(indexes)  # kept alive
+        arr = (ctypes.c_void_p * len(self.indexes))(*[ix.handle.value for ix in self.indexes])
+        cfg = gs_server_config()
+        cfg.lanes, cfg.max_batch, cfg.max_q_nnz, cfg.max_k = lanes, max_batch, max_q_nnz, max_k
+        cfg.max_wait_us, cfg.workspace_budget_bytes = max_wait_us, workspace_budget_bytes
+        if opts is not None:
+            cfg.opts = opts
+        h = ctypes.c_void_p()
+        _check(self._L.gs_server_create(arr, len(self.indexes), ctypes.byref(cfg), ctypes.byref(h)),
+               "gs_server_create")
+        self._h = h
+        self.max_k = max_k
+
+    def submit(self, index_id: int, terms, weights, k: int) -> int:
+        """terms: int32 numpy array, weights: float32 numpy array (host)."""
+        t = ctypes.c_int64(0)
+        _check(self._L.gs_server_submit(self._h, index_id, terms.ctypes.data, weights.ctypes.data, len(terms), k,
+                                        ctypes.byref(t)), "gs_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, k: int, score_dtype, timeout_us: int = 10_000_000):
+        """Returns (ids, scores, latency_us); raises GsError (GS_ERR_TIMEOUT) when the wait runs out."""
+        import numpy as np
+        ids = np.empty(k, np.int32)
+        sc = np.empty(k, np.int32 if score_dtype == torch.int32 else np.float32)
+        lat = ctypes.c_double(0)
+        _check(self._L.gs_server_wait(self._h, ticket, ids.ctypes.data, sc.ctypes.data, timeout_us, ctypes.byref(lat)),
+               "gs_server_wait")
+        return ids, sc, lat.value
+
+    def stats(self) -> dict:
+        st = gs_server_stats()
+        _check(self._L.gs_server_stats_get(self._h, ctypes.byref(st)), "gs_server_stats_get")
+        return {f: getattr(st, f) for f, _ in gs_server_stats._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._L.gs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

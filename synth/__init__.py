@@ -180,4 +180,7 @@ WORKLOADS = {
     # uneven batches over 8.84M docs: mixture query law, several batch sizes and k
     "docs8.8m_uneven": Workload("docs8.8m_uneven", N_8_8M, 1024, 1000, ("f32",), MIXTURE_LAW,
                                 {"batches": (1, 8, 64, 256, 1024), "ks": (10, 100, 1000)}),
+    # serving: 1M and 8.84M documents resident (FP16), Poisson arrivals at several rates
+    "serving_1m_8.8m": Workload("serving_1m_8.8m", N_8_8M, 256, 1000, ("f16",), MIXTURE_LAW,
+                                {"rates": (200, 1000, 2000, 5000), "seconds": 3.0}),
 }

@@ -327,3 +327,73 @@ def test_runner_graph_replay_matches_search():
         plan = runner.plan(8, 10)
         assert plan["tile_docs"] % 1024 == 0 and plan["tuned_ms"] > 0
         runner.free()
+
+
+def test_server_same_alone_and_in_the_mix():
+    """Continuous batching: every request's result is the same served alone and in a concurrent mix."""
+    import random
+    import threading
+    gs = _gs()
+    dev = _dev()
+    docs_a = synth.docs(40_000, seed=7)
+    docs_b = synth.docs(70_000, seed=8)
+    qs = synth.queries(48, seed=7, law=synth.MIXTURE_LAW)
+    idx = []
+    refs = []
+    for docs, impact in ((docs_a, "u8"), (docs_b, "f16")):
+        idx.append(gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                                     torch.from_numpy(docs.weights).to(dev), docs.vocab, impact))
+        refs.append((docs, oracle.OracleIndex.from_batch(docs, impact)))
+    server = gs.Server(idx, lanes=3, max_batch=16, max_q_nnz=4096, max_k=200, max_wait_us=200)
+    rng = random.Random(0)
+    reqs = [(i, rng.randrange(2), rng.choice([1, 10, 200])) for i in range(qs.n)]
+
+    def run(i, ix, k):
+        t, w = qs.row(i)
+        tk = server.submit(ix, np.ascontiguousarray(t), np.ascontiguousarray(w), k)
+        return server.wait(tk, k, idx[ix].score_dtype)
+
+    alone = {r: run(*r)[:2] for r in reqs}
+    mix = {}
+    lock = threading.Lock()
+
+    def worker(part):
+        tickets = []
+        for (i, ix, k) in part:
+            t, w = qs.row(i)
+            tickets.append(((i, ix, k), server.submit(ix, np.ascontiguousarray(t), np.ascontiguousarray(w), k)))
+        for key, tk in tickets:
+            out = server.wait(tk, key[2], idx[key[1]].score_dtype)
+            with lock:
+                mix[key] = out[:2]
+
+    order = reqs[:]
+    rng.shuffle(order)
+    threads = [threading.Thread(target=worker, args=(order[j::3],)) for j in range(3)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    st = server.stats()
+    assert st["completed"] == 2 * len(reqs) and st["batches"] < 2 * len(reqs)
+    for key in reqs:
+        (i, ix, k) = key
+        a_ids, a_sc = alone[key]
+        m_ids, m_sc = mix[key]
+        if ix == 0:  # uint8: bit-exact
+            assert np.array_equal(a_ids, m_ids) and np.array_equal(a_sc, m_sc)
+        else:
+            tol = 1e-5 * np.abs(a_sc) + 1e-6
+            assert np.all(np.abs(a_sc - m_sc) <= tol)
+        # and both match the oracle
+        docs, ref = refs[ix]
+        sub = qs.slice(i, i + 1)
+        rid, rsc, _ = ref.topk(sub.indptr, sub.terms, sub.weights, k)
+        if ix == 0:
+            check.check_u8(m_ids[None], m_sc[None], rid, rsc)
+        else:
+            check.check_float(ref, sub.indptr, sub.terms, sub.weights, m_ids[None], m_sc[None], rid, rsc, docs.n)
+    # bounded waits: an unknown ticket is an argument error, a wait that runs out is a timeout
+    with pytest.raises(gs.GsError):
+        server.wait(10 ** 9, 10, torch.float32, timeout_us=0)
+    server.close()
