@@ -42,7 +42,7 @@ constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting 
 constexpr int kMaxGroup = 256;               // queries per group (thresholds kept in shared memory)
 constexpr int kHeadG = 32;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 32;
-constexpr int kDefaultSampleStride = 16;
+constexpr int kDefaultSampleStride = 32;
 
 struct DtConfig {
   int G = 0, T = 0, m = 0, R = 0;  // R = 0: no sampling
