@@ -52,8 +52,8 @@ def _load():
         lib.synth_counts.restype = ctypes.c_int
         lib.synth_fill.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
-                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                   ctypes.c_int]
+                                   ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int]
         lib.synth_fill.restype = ctypes.c_int
         lib.synth_vocab_perm.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]
         lib.synth_vocab_perm.restype = ctypes.c_int
@@ -116,8 +116,12 @@ class SparseBatch:
 
 def generate(n: int, law: NnzLaw, *, vocab: int = VOCAB, zipf_s: float = 1.1, mu: float = -0.5,
              sigma: float = 0.8, wmax: float = 5.0, seed: int = 0, stream: int = STREAM_DOCS,
-             sort_terms: bool = True, threads: int = 0) -> SparseBatch:
-    """Draw n sparse vectors (see gen.c for the laws)."""
+             sort_terms: bool = True, threads: int = 0, perm_seed: int = 0) -> SparseBatch:
+    """Draw n sparse vectors (see gen.c for the laws).
+
+    seed selects the draws; perm_seed the vocabulary permutation shared by the
+    documents and queries of one collection.
+    """
     lib = _load()
     comp = law.packed()
     nnz = np.empty(n, dtype=np.int32)
@@ -130,17 +134,17 @@ def generate(n: int, law: NnzLaw, *, vocab: int = VOCAB, zipf_s: float = 1.1, mu
     total = int(indptr[-1])
     terms = np.empty(total, dtype=np.int32)
     w = np.empty(total, dtype=np.float32)
-    rc = lib.synth_fill(n, vocab, zipf_s, mu, sigma, wmax, seed, stream, indptr.ctypes.data,
+    rc = lib.synth_fill(n, vocab, zipf_s, mu, sigma, wmax, seed, perm_seed, stream, indptr.ctypes.data,
                         1 if sort_terms else 0, terms.ctypes.data, w.ctypes.data, threads)
     if rc != 0:
         raise ValueError(f"synth_fill failed ({rc})")
     return SparseBatch(indptr, terms, w, vocab)
 
 
-def vocab_perm(vocab: int = VOCAB, seed: int = 0) -> np.ndarray:
+def vocab_perm(vocab: int = VOCAB, perm_seed: int = 0) -> np.ndarray:
     """Zipf rank (0-based) -> term id, as used by generate()."""
     out = np.empty(vocab, dtype=np.int32)
-    if _load().synth_vocab_perm(vocab, seed, out.ctypes.data) != 0:
+    if _load().synth_vocab_perm(vocab, perm_seed, out.ctypes.data) != 0:
         raise ValueError("synth_vocab_perm failed")
     return out
 

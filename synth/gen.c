@@ -5,6 +5,10 @@
  * query sparse vectors over a fixed vocabulary).  Both the CPU oracle and the
  * GPU library consume its output; neither is used here.
  *
+ * The vocabulary permutation has its own seed (perm_seed): documents and
+ * queries drawn with different stream seeds share one rank -> term map, so
+ * frequent query terms are frequent document terms.
+ *
  * Laws (the paper's SPLADE statistics, Sec. 6.1, replaced by synthetic laws):
  *   - number of non-zeros per vector: a mixture of up to 4 components
  *     (Poisson(lambda) or uniform integer [a, b]), clamped to [lo, hi];
@@ -219,15 +223,15 @@ int synth_counts(int64_t n, uint64_t seed, uint64_t stream, int ncomp, const dou
  * synth_counts.  sort_terms != 0 sorts each row by term id (documents);
  * rows of queries keep their draw order. */
 int synth_fill(int64_t n, int32_t V, double zipf_s, double mu, double sigma, double wmax, uint64_t seed,
-               uint64_t stream, const int64_t* indptr, int sort_terms, int32_t* out_terms, float* out_w,
-               int nthreads) {
+               uint64_t perm_seed, uint64_t stream, const int64_t* indptr, int sort_terms, int32_t* out_terms,
+               float* out_w, int nthreads) {
   if (n < 0 || V < 2 || !indptr || !out_terms || !out_w || !(wmax > 0.0)) return SYN_ERR_ARG;
   for (int64_t i = 0; i < n; ++i) {
     int64_t len = indptr[i + 1] - indptr[i];
     if (len < 0 || len > V / 2) return SYN_ERR_ARG;
   }
   zipf_table z;
-  if (zipf_init(&z, V, zipf_s, seed) != SYN_OK) return SYN_ERR_NOMEM;
+  if (zipf_init(&z, V, zipf_s, perm_seed) != SYN_OK) return SYN_ERR_NOMEM;
   int err = SYN_OK;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);

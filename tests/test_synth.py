@@ -53,3 +53,12 @@ def test_query_laws():
     assert 0.03 < frac_long < 0.07
     expected_mean = 0.7 * 20 + 0.25 * 60 + 0.05 * 225
     assert abs(nnz.mean() - expected_mean) < 1.5
+
+
+def test_documents_and_queries_share_the_vocabulary_permutation():
+    """Queries drawn with another seed still put their frequent terms on frequent document terms."""
+    d = synth.docs(20000, seed=3)
+    df = np.bincount(d.terms, minlength=synth.VOCAB)
+    for seed in (0, 5, 11):
+        q = synth.queries(200, seed=seed)
+        assert df[q.terms].mean() > 0.2 * d.n
