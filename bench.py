@@ -127,6 +127,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's value (replicas: the job ends when the last rank does)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -317,11 +327,7 @@ def run_gpu(args, w, docs, qs, world, rank, local):
 
     # headline
     r, plan, idx = results[(head_imp, head_algo)]
-    span_s = r["span_ms"] / 1e3
-    if dist:
-        t = torch.tensor([span_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        span_s = float(t.item())
+    span_s = reduce_max_over_ranks(r["span_ms"] / 1e3, dist, dev)
     value = w.batch * args.steps * world / span_s
     st = idx.stats()
     # dominant kernel: the scoring stage (stage 3 -> 4)
@@ -514,6 +520,42 @@ def run_serving(args, w):
             "plain_fp32_batch500": plain, "results": out}
 
 
+def run_sweep(args, w):
+    """Document sparsity sweep (the paper's Table 5 set-up): term-parallel vs doc-tiled vs doc-parallel."""
+    import torch
+    from paper_2606_26441_gb300 import gpusparse as gs
+    gs.load()
+    dev = torch.device("cuda:0")
+    qs = synth.queries(w.batch, seed=0)
+    q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
+    out = []
+    for nnz in w.extra["doc_nnz"]:
+        law = synth.NnzLaw(((1.0, "uniform", nnz, nnz),), nnz, nnz)
+        docs = synth.docs(w.n_docs, seed=0, law=law, threads=cores())
+        idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                                torch.from_numpy(docs.weights).to(dev), docs.vocab, "f32", doc_major=True)
+        row = {"doc_nnz": nnz, "postings": docs.nnz}
+        for algo in ("term_parallel", "doc_tiled", "doc_parallel"):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_NUM_STAGE_EVENTS)]
+            for e in ev:
+                e.record()
+            o = gs.make_opts(algo, stage_events=ev)
+            ws = gs.alloc_workspace(idx, q.batch, q.nnz, w.k, o)
+            ts = []
+            for i in range(4):
+                gs.gs_search(idx, q, w.k, o, ws)
+                torch.cuda.synchronize()
+                if i:
+                    ts.append(ev[0].elapsed_time(ev[-1]))
+            row[algo + "_ms"] = float(np.median(ts))
+            del ws
+        out.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        idx.free()
+    return {"suite": "sparsity", "metric": "batch latency (ms) vs document non-zeros, top-1000",
+            "n_docs": w.n_docs, "batch": w.batch, "k": w.k, "results": out}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -521,6 +563,10 @@ def main():
     if w.extra.get("batches"):
         if rank == 0:
             print(json.dumps(run_uneven(args, w)), flush=True)
+        return
+    if w.extra.get("doc_nnz"):
+        if rank == 0:
+            print(json.dumps(run_sweep(args, w)), flush=True)
         return
     if w.extra.get("rates"):
         if rank == 0:

@@ -115,7 +115,9 @@ typedef struct {
                          doc-tiled kernel multiplies with FMAs instead of
                          scattering them; 0 = default (32), -1 = none,
                          at most GS_MAX_HEAD_TERMS */
-  int32_t reserved[6];
+  int32_t doc_major;  /* 1: also keep a document-major copy (doc CSR of stored
+                         impacts) for the DOC_PARALLEL kernel */
+  int32_t reserved[5];
 } gs_build_opts;
 
 typedef struct {
@@ -149,6 +151,9 @@ typedef struct {
   const int32_t* head_term;   /* [head_terms] term ids of the dense head */
   const void* head_dense;     /* [head_terms][head_ld] impacts (index type) */
   int64_t head_ld;            /* row length of head_dense, >= num_docs */
+  const int64_t* doc_indptr;  /* document-major copy (NULL unless built) */
+  const int32_t* doc_terms;
+  const void* doc_impacts;    /* stored impacts, index type */
 } gs_index_layout;
 
 /* Stage boundaries at which gs_search records the caller's CUDA events when
@@ -261,6 +266,19 @@ typedef struct {
 
 gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
                          const gs_search_opts* opts, gs_plan_info* out);
+
+/* Merge of per-shard top-k lists (documents sharded across GPUs or across
+ * indexes: each shard holds a contiguous range of document ids and returns
+ * local ids).  shard_ids[s] / shard_scores[s] point to [batch x k_in] device
+ * arrays of shard s, ordered as gs_search returns them; doc_offset[s] (host)
+ * is added to its ids.  Writes the global top-k (k <= n_shards * k_in,
+ * k <= GS_MAX_K) by (score desc, id asc) to out_ids / out_scores [batch x k]
+ * on the device.  Scores are float32, or int32 when score_is_int != 0.
+ * n_shards <= GS_MAX_SHARDS.  Asynchronous on `stream`. */
+#define GS_MAX_SHARDS 64
+gs_status gs_merge_topk(const int32_t* const* shard_ids, const void* const* shard_scores,
+                        const int64_t* doc_offset, int32_t n_shards, int32_t batch, int32_t k_in, int32_t k,
+                        int32_t score_is_int, int32_t* out_ids, void* out_scores, gs_stream_t stream);
 
 /* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits the last
  * call that used `workspace` raised. */

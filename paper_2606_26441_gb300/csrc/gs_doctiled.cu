@@ -655,7 +655,6 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   __shared__ int s_need;
   __shared__ int s_fill;
   const int q = blockIdx.x;
-  const int lane = threadIdx.x & 31;
   const uint32_t raw = cand_cnt[q];
   if (raw > cap && threadIdx.x == 0) atomicOr(flags, kFlagCandOverflow);
   const int64_t n = min((int64_t)raw, cap);
@@ -663,78 +662,8 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   if (threadIdx.x == 0) s_fill = 0;
   __syncthreads();
   if (n >= k) {
-    // radix select on the composite key (key << 32) | ~id: all distinct
-    uint64_t prefix = 0, pmask = 0;
-    int need = k;
-    int shift = 64;
-    bool done = false;
-    while (!done && shift > 0) {
-      const int bits = shift >= 11 ? 11 : shift;
-      shift -= bits;
-      const int nb = 1 << bits;
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-      __syncthreads();
-      const int64_t iters = (n + blockDim.x - 1) / blockDim.x;
-      for (int64_t itn = 0; itn < iters; ++itn) {
-        const int64_t i = itn * blockDim.x + threadIdx.x;
-        int bin = -1;
-        if (i < n) {
-          const uint2 v = c[i];
-          const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
-          if ((K & pmask) == prefix) bin = (int)((K >> shift) & (uint64_t)(nb - 1));
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-      }
-      __syncthreads();
-      // digit: walk bins from the top (nb <= 2048, two per thread)
-      const int per = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
-      int local = 0;
-      for (int u = 0; u < per; ++u) {
-        const int b = nb - 1 - ((int)threadIdx.x * per + u);
-        if (b >= 0) local += (int)hist[b];
-      }
-      int tot;
-      int acc = block_excl_scan(local, warp_buf, &tot);
-      for (int u = 0; u < per; ++u) {
-        const int b = nb - 1 - ((int)threadIdx.x * per + u);
-        if (b < 0) break;
-        const int h = (int)hist[b];
-        if (acc < need && need <= acc + h) {
-          s_digit = (uint32_t)b;
-          s_need = need - acc;
-        }
-        acc += h;
-      }
-      __syncthreads();
-      const uint32_t D = s_digit;
-      const int new_need = s_need;
-      __syncthreads();
-      prefix |= (uint64_t)D << shift;
-      pmask |= (uint64_t)(nb - 1) << shift;
-      // every key in bin D is taken: stop refining
-      if (new_need == (int)hist[D]) done = true;
-      need = new_need;
-      __syncthreads();
-    }
-    // take every candidate whose composite key, truncated to the resolved
-    // bits, is >= prefix: exactly k of them
-    const int64_t iters = (n + blockDim.x - 1) / blockDim.x;
-    for (int64_t itn = 0; itn < iters; ++itn) {
-      const int64_t i = itn * blockDim.x + threadIdx.x;
-      if (i < n) {
-        const uint2 v = c[i];
-        const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
-        if ((K & pmask) >= prefix) {
-          const int slot = atomicAdd(&s_fill, 1);
-          if (slot < k) {
-            ck[slot] = v.x;
-            cid[slot] = (int32_t)v.y;
-          }
-        }
-      }
-    }
-    __syncthreads();
+    select_topk_candidates([&](int64_t i) { return c[i]; }, n, k, hist, warp_buf, &s_digit, &s_need, &s_fill, ck,
+                           cid);
   } else {
     // all candidates, then the lowest-id ties at theta_q
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {

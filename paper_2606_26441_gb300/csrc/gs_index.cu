@@ -240,6 +240,19 @@ __global__ void head_fill_kernel(const uint8_t* __restrict__ blocks, const int64
   }
 }
 
+// document-major copy: the caller's doc CSR with stored (converted) impacts
+template <int IMPACT>
+__global__ void doc_major_kernel(const float* __restrict__ w, int64_t nnz, uint8_t* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const float x = w[p];
+    if (IMPACT == GS_IMPACT_F32) reinterpret_cast<float*>(out)[p] = x;
+    else if (IMPACT == GS_IMPACT_F16) reinterpret_cast<__half*>(out)[p] = __float2half_rn(x);
+    else if (IMPACT == GS_IMPACT_BF16) reinterpret_cast<__nv_bfloat16*>(out)[p] = __float2bfloat16_rn(x);
+    else out[p] = (uint8_t)quant_u8(x);
+  }
+}
+
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
@@ -284,6 +297,9 @@ static void free_index(gs_index* ix) {
   cudaFree(ix->head_term);
   cudaFree(ix->head_slot);
   cudaFree(ix->head_dense);
+  cudaFree(ix->dm_indptr);
+  cudaFree(ix->dm_terms);
+  cudaFree(ix->dm_impacts);
   delete ix;
 }
 
@@ -459,6 +475,31 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
     }
   }
+  if (opts && opts->doc_major) {
+    const int ib = impact_bytes(impact);
+    if ((e = cudaMalloc(&ix->dm_indptr, sizeof(int64_t) * (num_docs + 1))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&ix->dm_terms, sizeof(int32_t) * std::max<int64_t>(nnz, 1))) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaMalloc(&ix->dm_impacts, (size_t)ib * std::max<int64_t>(nnz, 1))) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(ix->dm_indptr, doc_indptr, sizeof(int64_t) * (num_docs + 1), cudaMemcpyDeviceToDevice,
+                             s)) != cudaSuccess)
+      return cuda_fail(e);
+    if (nnz > 0) {
+      if ((e = cudaMemcpyAsync(ix->dm_terms, doc_terms, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e);
+      const int grid = grid_for(nnz, 256, sms);
+      switch (impact) {
+        case GS_IMPACT_F32: doc_major_kernel<GS_IMPACT_F32><<<grid, 256, 0, s>>>(doc_w, nnz, ix->dm_impacts); break;
+        case GS_IMPACT_F16: doc_major_kernel<GS_IMPACT_F16><<<grid, 256, 0, s>>>(doc_w, nnz, ix->dm_impacts); break;
+        case GS_IMPACT_BF16: doc_major_kernel<GS_IMPACT_BF16><<<grid, 256, 0, s>>>(doc_w, nnz, ix->dm_impacts); break;
+        default: doc_major_kernel<GS_IMPACT_U8><<<grid, 256, 0, s>>>(doc_w, nnz, ix->dm_impacts); break;
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    ix->meta_bytes += (int64_t)(num_docs + 1) * 8 + nnz * (4 + ib);
+  }
   if ((e = cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
@@ -503,6 +544,9 @@ extern "C" gs_status gs_index_get_layout(const gs_index* ix, gs_index_layout* ou
   out->head_term = ix->head_term;
   out->head_dense = ix->head_dense;
   out->head_ld = ix->head_ld;
+  out->doc_indptr = ix->dm_indptr;
+  out->doc_terms = ix->dm_terms;
+  out->doc_impacts = ix->dm_impacts;
   return GS_OK;
 }
 

@@ -51,6 +51,10 @@ struct gs_index {
   int32_t* head_term = nullptr;    // H
   int32_t* head_slot = nullptr;    // V, -1 outside the head
   uint8_t* head_dense = nullptr;   // H * head_ld * impact_bytes
+  // document-major copy for the doc-parallel kernel (optional)
+  int64_t* dm_indptr = nullptr;    // N + 1
+  int32_t* dm_terms = nullptr;     // nnz
+  uint8_t* dm_impacts = nullptr;   // nnz * impact_bytes
   int64_t meta_bytes = 0;
   // host copies for planning
   std::vector<int64_t> h_term_block;

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "gs_docpar.cuh"
 #include "gs_doctiled.cuh"
 #include "gs_internal.cuh"
 #include "gs_topk.cuh"
@@ -335,7 +336,13 @@ extern "C" gs_status gs_search_workspace_size(const gs_index* ix, int32_t B, int
   if (st != GS_OK) return st;
   const int algo = resolve_algo(ix, opts);
   size_t tp_bytes = 0;
-  carve_tp(nullptr, ix, B, q_nnz, algo != GS_ALGO_DOC_TILED, &tp_bytes);
+  carve_tp(nullptr, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes);
+  if (algo == GS_ALGO_DOC_PARALLEL) {
+    size_t dp = 0;
+    st = dp_workspace_bytes(ix, B, &dp);
+    if (st != GS_OK) return st;
+    tp_bytes += dp;
+  }
   if (algo == GS_ALGO_DOC_TILED) {
     size_t dt = 0;
     st = dt_workspace_bytes(ix, B, q_nnz, std::max(k, 1), opts, &dt);
@@ -367,14 +374,17 @@ extern "C" gs_status gs_search(const gs_index* ix, const int32_t* q_indptr, cons
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int algo = resolve_algo(ix, opts);
   size_t tp_bytes = 0;
-  TpPlan p = carve_tp(workspace, ix, B, q_nnz, algo != GS_ALGO_DOC_TILED, &tp_bytes);
+  TpPlan p = carve_tp(workspace, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes);
   GS_CUDA_TRY(cudaMemsetAsync(p.hdr, 0, sizeof(Header), s));
+  if (algo == GS_ALGO_DOC_PARALLEL) {
+    return dp_search(ix, q_indptr, q_terms, q_w, B, q_nnz, k, out_ids, out_scores,
+                     static_cast<uint8_t*>(workspace) + tp_bytes, workspace_bytes - tp_bytes, &p.hdr->flags, opts, s);
+  }
   if (algo == GS_ALGO_DOC_TILED) {
     return dt_search(ix, q_indptr, q_terms, q_w, B, q_nnz, k, out_ids, out_scores,
                      static_cast<uint8_t*>(workspace) + tp_bytes, workspace_bytes - tp_bytes, &p.hdr->flags, opts,
                      s);
   }
-  if (algo == GS_ALGO_DOC_PARALLEL) return GS_ERR_UNSUPPORTED;
   const int chunk = (opts && opts->chunk_blocks > 0) ? opts->chunk_blocks : kDefaultChunkBlocks;
   st = run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, chunk, p.rows, p.ld, opts, s);
   if (st != GS_OK) return st;
@@ -444,6 +454,7 @@ extern "C" gs_status gs_search_plan(const gs_index* ix, int32_t B, int64_t q_nnz
   std::memset(out, 0, sizeof(*out));
   const int algo = resolve_algo(ix, opts);
   if (algo == GS_ALGO_DOC_TILED) return dt_plan_info(ix, B, k, opts, out);
+  if (algo == GS_ALGO_DOC_PARALLEL && !ix->dm_indptr) return GS_ERR_UNSUPPORTED;
   out->algo = algo;
   out->chunk_blocks = (opts && opts->chunk_blocks > 0) ? opts->chunk_blocks : kDefaultChunkBlocks;
   return GS_OK;

@@ -75,6 +75,87 @@ __device__ __forceinline__ void bitonic_sort_desc(uint32_t* key, int32_t* id, in
   __syncthreads();
 }
 
+// The k largest of n candidates by (key desc, id asc), found by a radix
+// select on the composite 64-bit key (key << 32) | ~id, which is distinct for
+// distinct ids.  get(i) returns candidate i as (key, id).  Leaves the k
+// winners, unordered, in ck / cid (shared memory) and returns after a
+// block-wide barrier.  Needs blockDim.x = 1024 and n >= k.
+template <class Get>
+__device__ __forceinline__ void select_topk_candidates(Get get, int64_t n, int k, uint32_t* hist, int* warp_buf,
+                                                       uint32_t* s_digit, int* s_need, int* s_fill, uint32_t* ck,
+                                                       int32_t* cid) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) *s_fill = 0;
+  __syncthreads();
+  uint64_t prefix = 0, pmask = 0;
+  int need = k;
+  int shift = 64;
+  bool done = false;
+  const int64_t iters = (n + blockDim.x - 1) / blockDim.x;
+  while (!done && shift > 0) {
+    const int bits = shift >= 11 ? 11 : shift;
+    shift -= bits;
+    const int nb = 1 << bits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int64_t itn = 0; itn < iters; ++itn) {
+      const int64_t i = itn * blockDim.x + threadIdx.x;
+      int bin = -1;
+      if (i < n) {
+        const uint2 v = get(i);
+        const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
+        if ((K & pmask) == prefix) bin = (int)((K >> shift) & (uint64_t)(nb - 1));
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    const int per = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
+    int local = 0;
+    for (int u = 0; u < per; ++u) {
+      const int b = nb - 1 - ((int)threadIdx.x * per + u);
+      if (b >= 0) local += (int)hist[b];
+    }
+    int tot;
+    int acc = block_excl_scan(local, warp_buf, &tot);
+    for (int u = 0; u < per; ++u) {
+      const int b = nb - 1 - ((int)threadIdx.x * per + u);
+      if (b < 0) break;
+      const int h = (int)hist[b];
+      if (acc < need && need <= acc + h) {
+        *s_digit = (uint32_t)b;
+        *s_need = need - acc;
+      }
+      acc += h;
+    }
+    __syncthreads();
+    const uint32_t D = *s_digit;
+    const int new_need = *s_need;
+    __syncthreads();
+    prefix |= (uint64_t)D << shift;
+    pmask |= (uint64_t)(nb - 1) << shift;
+    if (new_need == (int)hist[D]) done = true;  // every key in bin D is taken
+    need = new_need;
+    __syncthreads();
+  }
+  // every candidate whose composite key, cut to the resolved bits, is >= prefix
+  for (int64_t itn = 0; itn < iters; ++itn) {
+    const int64_t i = itn * blockDim.x + threadIdx.x;
+    if (i < n) {
+      const uint2 v = get(i);
+      const uint64_t K = ((uint64_t)v.x << 32) | (uint64_t)(~v.y);
+      if ((K & pmask) >= prefix) {
+        const int slot = atomicAdd(s_fill, 1);
+        if (slot < k) {
+          ck[slot] = v.x;
+          cid[slot] = (int32_t)v.y;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Top-k of `rows` dense rows: row r is S[r * ld .. r * ld + N).  Scores are
 // float (float paths) or int32 (uint8 path).  Output row-major [rows x k].
 template <typename ST>

@@ -30,7 +30,7 @@ EXPORTED = (
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
     "gs_search_plan", "gs_search_static", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
     "gs_runner_free", "gs_server_create", "gs_server_submit", "gs_server_wait", "gs_server_stats_get",
-    "gs_server_destroy",
+    "gs_server_destroy", "gs_merge_topk",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
 )
 GS_NUM_STAGE_EVENTS = 6
@@ -47,7 +47,8 @@ class GsError(RuntimeError):
 
 
 class gs_build_opts(ctypes.Structure):
-    _fields_ = [("tile_docs", ctypes.c_int32), ("head_terms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("tile_docs", ctypes.c_int32), ("head_terms", ctypes.c_int32), ("doc_major", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class gs_index_stats(ctypes.Structure):
@@ -61,7 +62,8 @@ class gs_index_stats(ctypes.Structure):
 class gs_index_layout(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_void_p), ("term_block", ctypes.c_void_p), ("term_len", ctypes.c_void_p),
                 ("max_score", ctypes.c_void_p), ("seg", ctypes.c_void_p), ("head_term", ctypes.c_void_p),
-                ("head_dense", ctypes.c_void_p), ("head_ld", ctypes.c_int64)]
+                ("head_dense", ctypes.c_void_p), ("head_ld", ctypes.c_int64), ("doc_indptr", ctypes.c_void_p),
+                ("doc_terms", ctypes.c_void_p), ("doc_impacts", ctypes.c_void_p)]
 
 
 class gs_search_opts(ctypes.Structure):
@@ -145,6 +147,9 @@ def load(path: str = LIB_PATH):
     L.gs_server_stats_get.restype = ctypes.c_int
     L.gs_server_destroy.argtypes = [P]
     L.gs_server_destroy.restype = None
+    L.gs_merge_topk.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64), I32, I32, I32, I32, I32,
+                                P, P, P]
+    L.gs_merge_topk.restype = ctypes.c_int
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -221,8 +226,9 @@ class Index:
 
     @staticmethod
     def build(doc_indptr: torch.Tensor, doc_terms: torch.Tensor, doc_w: torch.Tensor, vocab: int,
-              impact: str = "f32", tile_docs: int = 0, head_terms: int = 0, stream=None) -> "Index":
-        return gs_index_build(doc_indptr, doc_terms, doc_w, vocab, impact, tile_docs, head_terms, stream)
+              impact: str = "f32", tile_docs: int = 0, head_terms: int = 0, doc_major: bool = False,
+              stream=None) -> "Index":
+        return gs_index_build(doc_indptr, doc_terms, doc_w, vocab, impact, tile_docs, head_terms, doc_major, stream)
 
     @property
     def handle(self):
@@ -276,7 +282,7 @@ class Index:
 
 
 def gs_index_build(doc_indptr, doc_terms, doc_w, vocab: int, impact: str = "f32", tile_docs: int = 0,
-                   head_terms: int = 0, stream=None) -> Index:
+                   head_terms: int = 0, doc_major: bool = False, stream=None) -> Index:
     """Builds the index from device CSR tensors (int64 indptr, int32 terms, float32 weights)."""
     L = load()
     assert doc_indptr.dtype == torch.int64 and doc_terms.dtype == torch.int32 and doc_w.dtype == torch.float32
@@ -284,6 +290,7 @@ def gs_index_build(doc_indptr, doc_terms, doc_w, vocab: int, impact: str = "f32"
     o = gs_build_opts()
     o.tile_docs = tile_docs
     o.head_terms = head_terms
+    o.doc_major = 1 if doc_major else 0
     _check(L.gs_index_build_ex(_ptr(doc_indptr), _ptr(doc_terms), _ptr(doc_w), doc_indptr.numel() - 1,
                                doc_terms.numel(), vocab, IMPACTS[impact], ctypes.byref(o), _stream(stream),
                                ctypes.byref(h)), "gs_index_build")
@@ -456,6 +463,22 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def gs_merge_topk(shard_ids, shard_scores, doc_offsets, k: int, stream=None):
+    """Global top-k from per-shard [B, k_in] device results; doc_offsets: first global id of each shard."""
+    L = load()
+    S = len(shard_ids)
+    B, k_in = shard_ids[0].shape
+    ids = (ctypes.c_void_p * S)(*[t.data_ptr() for t in shard_ids])
+    scs = (ctypes.c_void_p * S)(*[t.data_ptr() for t in shard_scores])
+    offs = (ctypes.c_int64 * S)(*[int(o) for o in doc_offsets])
+    is_int = shard_scores[0].dtype == torch.int32
+    out_ids = torch.empty((B, k), dtype=torch.int32, device=shard_ids[0].device)
+    out_sc = torch.empty((B, k), dtype=shard_scores[0].dtype, device=shard_ids[0].device)
+    _check(L.gs_merge_topk(ids, scs, offs, S, B, k_in, k, 1 if is_int else 0, _ptr(out_ids), _ptr(out_sc),
+                           _stream(stream)), "gs_merge_topk")
+    return out_ids, out_sc
 
 
 def gs_version() -> int:

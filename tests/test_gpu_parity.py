@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 ALGOS = ["term_parallel", "doc_tiled"]
 # the doc-tiled kernel with and without the dense head
 VARIANTS = [("term_parallel", {}), ("doc_tiled", {}), ("doc_tiled", {"use_head": -1}),
-            ("doc_tiled", {"use_head": 1})]
+            ("doc_tiled", {"use_head": 1}), ("doc_parallel", {})]
 
 
 def _gs():
@@ -50,13 +50,13 @@ def _cudart():
 class Case:
     """A collection + query batch + GPU index + oracle index for one impact type."""
 
-    def __init__(self, docs, qs, impact, tile_docs=0, head_terms=0):
+    def __init__(self, docs, qs, impact, tile_docs=0, head_terms=0, doc_major=True):
         gs = _gs()
         dev = _dev()
         self.docs, self.qs, self.impact = docs, qs, impact
         self.idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
                                      torch.from_numpy(docs.weights).to(dev), docs.vocab, impact, tile_docs,
-                                     head_terms)
+                                     head_terms, doc_major)
         self.q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
         self.ref = oracle.OracleIndex.from_batch(docs, impact)
 
@@ -397,3 +397,38 @@ def test_server_same_alone_and_in_the_mix():
     with pytest.raises(gs.GsError):
         server.wait(10 ** 9, 10, torch.float32, timeout_us=0)
     server.close()
+
+
+def test_sharded_merge_equals_unsharded():
+    """Documents split into virtual shards (contiguous id ranges, local ids), searched
+    separately and merged on the GPU: the same top-k as one index (bit-exact on uint8)."""
+    gs = _gs()
+    dev = _dev()
+    docs = synth.docs(90_001, seed=10)
+    qs = synth.queries(24, seed=10)
+    cuts = [0, 20_000, 50_000, 51_000, docs.n]  # uneven shards, one tiny
+    for impact in ("u8", "f32"):
+        full = Case(docs, qs, impact)
+        for k in (10, 1000):
+            ref_ids, ref_sc = gs.gs_search(full.idx, full.q, k)
+            sid, ssc, shards = [], [], []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                sub = docs.slice(a, b)
+                c = Case(sub, qs, impact)
+                kk = min(k, sub.n)
+                i_, s_ = gs.gs_search(c.idx, c.q, kk)
+                sid.append(i_.contiguous())
+                ssc.append(s_.contiguous())
+                shards.append(c)
+            # shards with fewer than k documents return all of them: pad the others to a common k_in
+            k_in = min(x.shape[1] for x in sid)
+            ids, sc = gs.gs_merge_topk([x[:, :k_in].contiguous() for x in sid], [x[:, :k_in].contiguous() for x in ssc],
+                                       cuts[:-1], min(k, k_in * len(sid)))
+            torch.cuda.synchronize()
+            kk = ids.shape[1]
+            if impact == "u8":
+                assert torch.equal(ids.cpu(), ref_ids.cpu()[:, :kk]) and torch.equal(sc.cpu(), ref_sc.cpu()[:, :kk])
+            else:
+                rid, rsc, _ = full.ref.topk(qs.indptr, qs.terms, qs.weights, kk)
+                check.check_float(full.ref, qs.indptr, qs.terms, qs.weights, ids.cpu().numpy(), sc.cpu().numpy(),
+                                  rid, rsc, docs.n)
