@@ -33,15 +33,15 @@
 namespace gs {
 namespace {
 
-constexpr int kDtThreads = 1024;
-constexpr int kDtMaxAccBytes = 128 * 1024;  // G x T accumulators
-constexpr int kEntCap = 2048;                // query entries staged in shared memory (16 KB)
-constexpr int kItemCap = 9216;               // (term, 128-posting chunk) items per term batch (18 KB)
+constexpr int kDtThreads = 512;                  // two CTAs per SM (64 registers each)
+constexpr int kDtMaxAccBytes = 64 * 1024;     // G x T accumulators
+constexpr int kEntCap = 1536;                // query entries staged in shared memory (12 KB)
+constexpr int kItemCap = 4608;               // (term, 128-posting chunk) items per term batch (9 KB)
 constexpr int kTinySeg = 64;                 // segments shorter than this are packed, not itemised
 constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting chunks per term batch
-constexpr int kMaxGroup = 256;               // queries per group (thresholds kept in shared memory)
-constexpr int kHeadG = 32;                   // queries per group when the dense head is used
-constexpr int kDefaultGroup = 32;
+constexpr int kMaxGroup = 64;                // queries per group (thresholds kept in shared memory)
+constexpr int kHeadG = 16;                   // queries per group when the dense head is used
+constexpr int kDefaultGroup = 16;
 constexpr int kDefaultSampleStride = 32;
 
 struct DtConfig {
@@ -56,7 +56,8 @@ struct DtConfig {
 gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts, DtConfig* c) {
   if (!ix->seg) return GS_ERR_UNSUPPORTED;
   c->T = (opts && opts->tile_docs > 0) ? opts->tile_docs : ix->tile_docs;
-  if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0) return GS_ERR_INVALID_ARG;
+  // a power of two; at most 64 chunks of 128 documents per row
+  if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0 || c->T > 8192) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
   // the dense head keeps one accumulator register per query of the group
@@ -97,8 +98,7 @@ struct DtPlan {
   int32_t* n_u;       // [ng]
   uint2* ent;         // [q_nnz] (query within group, weight bits)
   uint32_t* samp;     // [B][sample_docs]
-  int32_t* samp_ids;  // [B][k]
-  uint32_t* samp_sc;  // [B][k]
+  uint32_t* theta;    // [B] k-th largest sample score (raw bits)
   uint2* cand;        // [B][cap] (key, doc)
   uint32_t* cand_cnt; // [B]
   uint32_t* tiebm;    // [B][bm_words]
@@ -116,8 +116,7 @@ DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const
   p.n_u = cv.take<int32_t>(c.ng);
   p.ent = cv.take<uint2>(q_nnz + 1);
   p.samp = cv.take<uint32_t>((size_t)B * std::max<int64_t>(c.sample_docs, 1));
-  p.samp_ids = cv.take<int32_t>((size_t)B * k);
-  p.samp_sc = cv.take<uint32_t>((size_t)B * k);
+  p.theta = cv.take<uint32_t>(B);
   p.cand = cv.take<uint2>((size_t)B * c.cap);
   p.cand_cnt = cv.take<uint32_t>(B);
   p.tiebm = cv.take<uint32_t>((size_t)B * c.bm_words);
@@ -239,9 +238,9 @@ enum { kModeSample = 0, kModeMain = 1 };
 
 // theta_q: key of the k-th largest sample score (stored as raw score bits)
 template <typename AccT>
-__device__ __forceinline__ uint32_t theta_key(const uint32_t* samp_sc, int64_t q, int k, int R) {
+__device__ __forceinline__ uint32_t theta_key(const uint32_t* theta, int64_t q, int R) {
   if (R <= 0) return 0u;  // no sampling: every document is a candidate
-  const uint32_t raw = __ldg(samp_sc + q * k + (k - 1));
+  const uint32_t raw = __ldg(theta + q);
   if (std::is_same<AccT, float>::value) return score_key(__uint_as_float(raw));
   return score_key((int32_t)raw);
 }
@@ -255,13 +254,13 @@ __device__ __forceinline__ uint32_t theta_key(const uint32_t* samp_sc, int64_t q
 // documents for dense terms: no bank conflicts), and every loaded posting
 // serves all of the group's queries holding the term.
 template <int IMPACT, int MODE, bool HEAD>
-__global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
+__global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const uint32_t* __restrict__ seg,
     int seg_tiles, int64_t N, const int32_t* __restrict__ q_indptr, int32_t B, int32_t q_nnz, int G, int T,
     int m, int R,
     int ng, int n_sample, const int32_t* __restrict__ u_terms, const int32_t* __restrict__ u_ptr,
     const int32_t* __restrict__ n_u, const uint2* __restrict__ ent, uint32_t* __restrict__ samp,
-    int64_t sample_docs, const uint32_t* __restrict__ samp_sc, int k, uint2* __restrict__ cand,
+    int64_t sample_docs, const uint32_t* __restrict__ theta, int k, uint2* __restrict__ cand,
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
     const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
     const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact) {
@@ -304,8 +303,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
   }
   if (MODE == kModeMain)
-    for (int i = threadIdx.x; i < gq; i += blockDim.x)
-      s_theta[i] = R > 0 ? __ldg(samp_sc + (int64_t)(q0 + i) * k + (k - 1)) : 0u;
+    for (int i = threadIdx.x; i < gq; i += blockDim.x) s_theta[i] = R > 0 ? __ldg(theta + q0 + i) : 0u;
   const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
   const int nterm = n_u[g];
   const int32_t* ut = u_terms + ebase;
@@ -469,9 +467,12 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
     // 1024-document slab, p = 32 (w / 2) + l: the head rows are read
     // coalesced, four rows in flight, the weights are warp-wide broadcasts,
     // and every (query, document) cell has one owner (no atomics).
-    const int qh = warp & 1;
-    const int dp = (warp >> 1) * 32 + lane;
-    for (int slab = 0; slab < T; slab += 1024) {
+    // kHeadG / 16 warps share a document pair range; one slab = kSlab documents
+    constexpr int kQH = kHeadG / 16;
+    constexpr int kSlab = 2 * kDtThreads / kQH;
+    const int qh = warp % kQH;
+    const int dp = (warp / kQH) * 32 + lane;
+    for (int slab = 0; slab < T; slab += kSlab) {
       if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
       const int64_t col = doc0 + slab + 2 * dp;
       AccT r[16][2];
@@ -542,55 +543,82 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
 
   // epilogue: each warp step covers 128 documents of one query row (4 per lane)
   const int cpr = T / 128;  // chunks per row
-  for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
-    const int ql = ci / cpr;
-    const int d0 = (ci - ql * cpr) * 128 + lane * 4;
-    const uint4 raw = *reinterpret_cast<const uint4*>(acc + ql * T + d0);
-    if (MODE == kModeSample) {
-      *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) = raw;
-      continue;
+  if (MODE == kModeSample) {
+    for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
+      const int ql = ci / cpr;
+      const int d0 = (ci - ql * cpr) * 128 + lane * 4;
+      *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
+          *reinterpret_cast<const uint4*>(acc + ql * T + d0);
     }
+    return;
+  }
+  // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
+  // whole query rows: it counts the row's candidates, reserves the row's
+  // slots with one global atomic, then writes them; no block barrier.
+  for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
     const int q = q0 + ql;
-    const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
     const uint32_t th = s_theta[ql];
-    unsigned gtm = 0, eqm = 0;
+    const AccT* row = acc + ql * T;
+    auto masks = [&](int d0, uint4& raw, unsigned& gtm, unsigned& eqm) {
+      raw = *reinterpret_cast<const uint4*>(row + d0);
+      const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+      gtm = 0;
+      eqm = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const bool in = doc0 + d0 + i < N;
-      bool gt, eq;
-      if (R <= 0) {
-        gt = in;
-        eq = false;
-      } else if (IMPACT == GS_IMPACT_U8) {
-        gt = in && (int32_t)rv[i] > (int32_t)th;
-        eq = in && (int32_t)rv[i] == (int32_t)th;
-      } else {
-        gt = in && __uint_as_float(rv[i]) > __uint_as_float(th);
-        eq = in && __uint_as_float(rv[i]) == __uint_as_float(th);
+      for (int i = 0; i < 4; ++i) {
+        const bool in = doc0 + d0 + i < N;
+        bool gt, eq;
+        if (R <= 0) {
+          gt = in;
+          eq = false;
+        } else if (IMPACT == GS_IMPACT_U8) {
+          gt = in && (int32_t)rv[i] > (int32_t)th;
+          eq = in && (int32_t)rv[i] == (int32_t)th;
+        } else {
+          gt = in && __uint_as_float(rv[i]) > __uint_as_float(th);
+          eq = in && __uint_as_float(rv[i]) == __uint_as_float(th);
+        }
+        gtm |= (unsigned)gt << i;
+        eqm |= (unsigned)eq << i;
       }
-      gtm |= (unsigned)gt << i;
-      eqm |= (unsigned)eq << i;
+    };
+    // pass 1: candidates of the row, and which 128-document chunks need pass 2
+    unsigned cnt = 0;
+    uint64_t chunk_hits = 0;
+    for (int c = 0; c < cpr; ++c) {
+      uint4 raw;
+      unsigned gtm, eqm;
+      masks(c * 128 + lane * 4, raw, gtm, eqm);
+      cnt += (unsigned)__popc(gtm);
+      if (__any_sync(0xffffffffu, (gtm | eqm) != 0)) chunk_hits |= 1ull << c;
     }
-    // tie bitmap: 8 lanes x 4 documents make one 32-bit word
-    unsigned word = eqm << (4 * (lane & 7));
-    word |= __shfl_xor_sync(0xffffffffu, word, 1);
-    word |= __shfl_xor_sync(0xffffffffu, word, 2);
-    word |= __shfl_xor_sync(0xffffffffu, word, 4);
-    const int64_t wdoc = doc0 + (d0 - (lane & 7) * 4);
-    if ((lane & 7) == 0 && wdoc < N) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
-    if (__any_sync(0xffffffffu, gtm != 0)) {
-      const int cnt = __popc(gtm);
-      int incl = cnt;
+    const unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
+    uint32_t base = 0;
+    if (lane == 0 && tot) base = atomicAdd(&cand_cnt[q], tot);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    // pass 2: tie words and candidate writes, chunks with hits only
+    for (int c = 0; c < cpr; ++c) {
+      if (!(chunk_hits & (1ull << c))) continue;
+      const int d0 = c * 128 + lane * 4;
+      uint4 raw;
+      unsigned gtm, eqm;
+      masks(d0, raw, gtm, eqm);
+      unsigned word = eqm << (4 * (lane & 7));
+      word |= __shfl_xor_sync(0xffffffffu, word, 1);
+      word |= __shfl_xor_sync(0xffffffffu, word, 2);
+      word |= __shfl_xor_sync(0xffffffffu, word, 4);
+      const int64_t wdoc = doc0 + (d0 - (lane & 7) * 4);
+      if ((lane & 7) == 0 && word && wdoc < N) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+      const int n_gt = __popc(gtm);
+      int incl = n_gt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      uint32_t basec = 0;
-      if (lane == 0) basec = atomicAdd(&cand_cnt[q], (uint32_t)tot);
-      basec = __shfl_sync(0xffffffffu, basec, 0);
-      uint32_t slot = basec + (uint32_t)(incl - cnt);
+      uint32_t slot = base + (uint32_t)(incl - n_gt);
+      base += (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         if (gtm & (1u << i)) {
@@ -607,12 +635,12 @@ __global__ void __launch_bounds__(kDtThreads, 1) dt_tile_kernel(
 // Candidates of the sample tiles (their scores sit in the sample rows).
 template <typename ST>
 __global__ void dt_sample_emit_kernel(const uint32_t* __restrict__ samp, int64_t sample_docs, int T, int R,
-                                      const uint32_t* __restrict__ samp_sc, int k, uint2* __restrict__ cand,
+                                      const uint32_t* __restrict__ theta_bits, int k, uint2* __restrict__ cand,
                                       uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm,
                                       int64_t bm_words) {
   const int q = blockIdx.y;
   const int lane = threadIdx.x & 31;
-  const uint32_t theta = theta_key<ST>(samp_sc, q, k, R);
+  const uint32_t theta = theta_key<ST>(theta_bits, q, R);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // uniform per warp: chunks of 32 consecutive sample positions
   for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < sample_docs; i0 += stride) {
@@ -626,7 +654,7 @@ __global__ void dt_sample_emit_kernel(const uint32_t* __restrict__ samp, int64_t
     const bool gt = key > theta, tie = key == theta;
     const unsigned mgt = __ballot_sync(0xffffffffu, gt);
     const unsigned mtie = __ballot_sync(0xffffffffu, tie);
-    if (lane == 0) tiebm[(int64_t)q * bm_words + (doc >> 5)] = mtie;
+    if (lane == 0 && mtie) tiebm[(int64_t)q * bm_words + (doc >> 5)] = mtie;
     if (mgt) {
       uint32_t base = 0;
       if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)__popc(mgt));
@@ -644,7 +672,7 @@ template <typename ST>
 __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict__ cand,
                                                         const uint32_t* __restrict__ cand_cnt, int64_t cap,
                                                         const uint32_t* __restrict__ tiebm, int64_t bm_words,
-                                                        int64_t N, const uint32_t* __restrict__ samp_sc, int R,
+                                                        int64_t N, const uint32_t* __restrict__ theta_bits, int R,
                                                         int k, int32_t* __restrict__ out_ids,
                                                         ST* __restrict__ out_scores, uint32_t* flags) {
   __shared__ uint32_t hist[2048];
@@ -670,7 +698,7 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
       ck[i] = c[i].x;
       cid[i] = (int32_t)c[i].y;
     }
-    const uint32_t theta = theta_key<ST>(samp_sc, q, k, R);
+    const uint32_t theta = theta_key<ST>(theta_bits, q, R);
     const int need_t = k - (int)n;
     int taken = 0;
     const uint32_t* bm = tiebm + (int64_t)q * bm_words;
@@ -734,19 +762,17 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
   if (c.R > 0) {
     ks<<<c.n_sample * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N,
                                                    q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample,
-                                                   p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.samp_sc,
+                                                   p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta,
                                                    k, p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->head_dense,
                                                    ix->head_ld, c.H, p.headw, p.head_act, p.head_nact);
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
-      topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.samp),
-                                                                c.sample_docs, c.sample_docs, k, p.samp_ids,
-                                                                reinterpret_cast<int32_t*>(p.samp_sc));
+      kth_score_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.samp),
+                                                               c.sample_docs, c.sample_docs, k, p.theta);
     else
-      topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const float*>(p.samp),
-                                                              c.sample_docs, c.sample_docs, k, p.samp_ids,
-                                                              reinterpret_cast<float*>(p.samp_sc));
+      kth_score_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const float*>(p.samp), c.sample_docs,
+                                                             c.sample_docs, k, p.theta);
     GS_LAUNCH_CHECK();
   } else {
     record_stage(opts, 2, s);
@@ -754,7 +780,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
   record_stage(opts, 3, s);
   km<<<c.nt * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B,
                                            q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u,
-                                           p.ent, p.samp, c.sample_docs, p.samp_sc, k, p.cand, p.cand_cnt, c.cap,
+                                           p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
                                            p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act,
                                            p.head_nact);
   GS_LAUNCH_CHECK();
@@ -811,6 +837,7 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
                                        p.head_nact, flags);
   GS_LAUNCH_CHECK();
   GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
+  GS_CUDA_TRY(cudaMemsetAsync(p.tiebm, 0, sizeof(uint32_t) * (size_t)B * c.bm_words, s));
   record_stage(opts, 1, s);
   switch (ix->impact) {
     case GS_IMPACT_F32: st = launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
@@ -822,18 +849,18 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   if (c.R > 0) {
     dim3 grid((unsigned)std::min<int64_t>((c.sample_docs + 255) / 256, 64), (unsigned)B);
     if (ix->impact == GS_IMPACT_U8)
-      dt_sample_emit_kernel<int32_t><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.samp_sc, k, p.cand,
+      dt_sample_emit_kernel<int32_t><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.theta, k, p.cand,
                                                           p.cand_cnt, c.cap, p.tiebm, c.bm_words);
     else
-      dt_sample_emit_kernel<float><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.samp_sc, k, p.cand,
+      dt_sample_emit_kernel<float><<<grid, 256, 0, s>>>(p.samp, c.sample_docs, c.T, c.R, p.theta, k, p.cand,
                                                         p.cand_cnt, c.cap, p.tiebm, c.bm_words);
     GS_LAUNCH_CHECK();
   }
   if (ix->impact == GS_IMPACT_U8)
-    dt_final_kernel<int32_t><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.samp_sc,
+    dt_final_kernel<int32_t><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
                                                 c.R, k, out_ids, static_cast<int32_t*>(out_scores), flags);
   else
-    dt_final_kernel<float><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.samp_sc,
+    dt_final_kernel<float><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
                                               c.R, k, out_ids, static_cast<float*>(out_scores), flags);
   GS_LAUNCH_CHECK();
   record_stage(opts, 5, s);

@@ -74,11 +74,11 @@ std::vector<gs_search_opts> candidates(const gs_index* ix, const gs_search_opts&
   }
   const int T0 = ix->tile_docs;
   for (int T = T0; T <= 4096; T *= 2) {
-    for (int G : {8, 16, 32}) {
-      if ((int64_t)G * T > 32768) continue;
-      if (G > bucket && G != 8) continue;
+    for (int G : {4, 8, 16}) {
+      if ((int64_t)G * T > 16384) continue;
+      if (G > bucket && G != 4) continue;
       for (int head : {1, -1}) {
-        if (head == 1 && (G != 32 || ix->head_H == 0)) continue;
+        if (head == 1 && (G != 16 || ix->head_H == 0)) continue;
         for (int R : {16, 32, 64}) {
           gs_search_opts o = base;
           o.algo = GS_ALGO_DOC_TILED;

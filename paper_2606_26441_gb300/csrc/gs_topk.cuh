@@ -156,29 +156,17 @@ __device__ __forceinline__ void select_topk_candidates(Get get, int64_t n, int k
   __syncthreads();
 }
 
-// Top-k of `rows` dense rows: row r is S[r * ld .. r * ld + N).  Scores are
-// float (float paths) or int32 (uint8 path).  Output row-major [rows x k].
+// The k-th largest 32-bit key of row r[0..N) (radix select, 11 + 11 + 10 bit
+// digits, one histogram pass over the row per digit).  *need_out receives how
+// many keys equal to it belong to the top k.  blockDim.x must be 1024.
 template <typename ST>
-__global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST* __restrict__ S, int64_t ld,
-                                                                       int64_t N, int k,
-                                                                       int32_t* __restrict__ out_ids,
-                                                                       ST* __restrict__ out_scores) {
-  // the histograms and, after the radix passes, the k candidates share storage
-  __shared__ uint32_t smem_raw[kHistCopies * 2048];
-  static_assert(2 * GS_MAX_K <= kHistCopies * 2048, "candidates must fit in the histogram storage");
-  uint32_t(*hist)[2048] = reinterpret_cast<uint32_t(*)[2048]>(smem_raw);
-  uint32_t* cand_key = smem_raw;
-  int32_t* cand_id = reinterpret_cast<int32_t*>(smem_raw + GS_MAX_K);
-  __shared__ int warp_buf[32];
-  __shared__ uint32_t s_digit;
-  __shared__ int s_need;
-  __shared__ int s_gt;
-
-  const int row = blockIdx.x;
-  const ST* __restrict__ r = S + (int64_t)row * ld;
+__device__ __forceinline__ uint32_t radix_kth_key(const ST* __restrict__ r, int64_t N, int k,
+                                                  uint32_t (*hist)[2048], int* warp_buf, uint32_t* s_digit_p,
+                                                  int* s_need_p, int* need_out) {
+  uint32_t& s_digit = *s_digit_p;
+  int& s_need = *s_need_p;
   const int lane = threadIdx.x & 31;
   const int copy = (threadIdx.x >> 5) % kHistCopies;
-
   uint32_t prefix = 0, pmask = 0;
   int need = k;
   for (int pass = 0; pass < 3; ++pass) {
@@ -231,6 +219,33 @@ __global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST*
       __syncthreads();
     }
   }
+  *need_out = need;
+  return prefix;
+}
+
+// Top-k of `rows` dense rows: row r is S[r * ld .. r * ld + N).  Scores are
+// float (float paths) or int32 (uint8 path).  Output row-major [rows x k].
+template <typename ST>
+__global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST* __restrict__ S, int64_t ld,
+                                                                       int64_t N, int k,
+                                                                       int32_t* __restrict__ out_ids,
+                                                                       ST* __restrict__ out_scores) {
+  // the histograms and, after the radix passes, the k candidates share storage
+  __shared__ uint32_t smem_raw[kHistCopies * 2048];
+  static_assert(2 * GS_MAX_K <= kHistCopies * 2048, "candidates must fit in the histogram storage");
+  uint32_t(*hist)[2048] = reinterpret_cast<uint32_t(*)[2048]>(smem_raw);
+  uint32_t* cand_key = smem_raw;
+  int32_t* cand_id = reinterpret_cast<int32_t*>(smem_raw + GS_MAX_K);
+  __shared__ int warp_buf[32];
+  __shared__ uint32_t s_digit;
+  __shared__ int s_need;
+  __shared__ int s_gt;
+
+  const int row = blockIdx.x;
+  const ST* __restrict__ r = S + (int64_t)row * ld;
+
+  int need = k;
+  const uint32_t prefix = radix_kth_key(r, N, k, hist, warp_buf, &s_digit, &s_need, &need);
   // prefix is now the k-th largest key; `need` ties at it are taken (lowest ids)
   const uint32_t theta = prefix;
   const int n_gt = k - need;
@@ -275,6 +290,25 @@ __global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST*
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     out_ids[(int64_t)row * k + j] = cand_id[j];
     out_scores[(int64_t)row * k + j] = key_to_score<ST>(cand_key[j]);
+  }
+}
+
+// The k-th largest score of each of `rows` dense rows (raw score bits), no
+// collection or sort: the threshold the doc-tiled path needs from its sample.
+template <typename ST>
+__global__ void __launch_bounds__(kTopkThreads) kth_score_rows_kernel(const ST* __restrict__ S, int64_t ld, int64_t N,
+                                                                      int k, uint32_t* __restrict__ out_bits) {
+  __shared__ uint32_t hist[kHistCopies][2048];
+  __shared__ int warp_buf[32];
+  __shared__ uint32_t s_digit;
+  __shared__ int s_need;
+  int need = k;
+  const uint32_t key = radix_kth_key(S + (int64_t)blockIdx.x * ld, N, k, hist, warp_buf, &s_digit, &s_need, &need);
+  if (threadIdx.x == 0) {
+    const ST v = key_to_score<ST>(key);
+    uint32_t bits;
+    memcpy(&bits, &v, 4);
+    out_bits[blockIdx.x] = bits;
   }
 }
 
