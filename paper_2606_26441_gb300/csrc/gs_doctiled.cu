@@ -374,54 +374,31 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     const int units = total + packed;
-    int nxt = 0;
-    if (lane == 0) nxt = atomicAdd(&s_next, 1);
-    nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    while (nxt < units) {
-      const int it = nxt;
-      if (lane == 0) nxt = atomicAdd(&s_next, 1);
-      nxt = __shfl_sync(0xffffffffu, nxt, 0);
-      if (it >= total) {
-        // 32 postings of the packed short segments: one posting per lane, its
-        // own term and entries
-        const int P = (it - total) * 32 + lane;
-        if (P < tiny_total) {
-          int jj = chunk_j0[it - total];
-          while (P >= s_tp[jj + 1]) ++jj;
-          const int rel = P - s_tp[jj] + s_off[jj];
-          const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
-          const int li = rel & 31;
-          const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
-          const uint32_t da = (uint32_t)(doc - doc0) * 4u;
-          AccT xv;
-          if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
-          else xv = (AccT)load_x<IMPACT>(blk, li);
-          const int32_t eb = s_e0[jj], ee = s_e1[jj];
-          for (int32_t en = eb; en < ee; ++en) {
-            uint2 E;
-            if (staged) {
-              E = ent_s[en - ent_lo];
-            } else {
-              E = __ldg(ent + en);
-              E.x *= row_bytes;
-            }
-            const uint32_t addr = acc_s + E.x + da;
-            if (IMPACT == GS_IMPACT_U8)
-              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)E.y * (int32_t)xv) : "memory");
-            else
-              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(E.y) * (float)xv)
-                           : "memory");
-          }
-        }
-        continue;
+    // one (query, weight) entry of the group
+    auto entry = [&](int32_t en) {
+      uint2 E;
+      if (staged) {
+        E = ent_s[en - ent_lo];
+      } else {
+        E = __ldg(ent + en);
+        E.x *= row_bytes;
       }
+      return E;
+    };
+    auto red = [&](uint32_t addr, uint32_t wbits, AccT xv) {
+      if (IMPACT == GS_IMPACT_U8)
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
+      else
+        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
+    };
+    // item it: lane l loads posting l of each of its 4 blocks; da = byte
+    // offset of the document inside a row, -1 when the lane has no posting
+    auto load_item = [&](int it, int* da, AccT* x) -> int {
       const int jj = item_term[it];
       const int c = it - s_item[jj];
       const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
       const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
       const uint32_t len = (uint32_t)s_len[jj];
-      int da[4];  // byte offset of the document inside a row, -1 when the lane has no posting
-      AccT x[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         da[i] = -1;
@@ -434,26 +411,69 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           else x[i] = (AccT)load_x<IMPACT>(blk, lane);
         }
       }
+      return jj;
+    };
+    // NI loaded items of term jj: every entry of the term, every posting
+    auto score_items = [&](int jj, const int* da, const AccT* x, int ni) {
       const int32_t eb = s_e0[jj], ee = s_e1[jj];
       for (int32_t en = eb; en < ee; ++en) {
-        uint2 E;
-        if (staged) {
-          E = ent_s[en - ent_lo];
-        } else {
-          E = __ldg(ent + en);
-          E.x *= row_bytes;
-        }
+        const uint2 E = entry(en);
         const uint32_t row = acc_s + E.x;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (da[i] >= 0) {
-            const uint32_t addr = row + (uint32_t)da[i];
-            if (IMPACT == GS_IMPACT_U8) {
-              asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)E.y * (int32_t)x[i]) : "memory");
-            } else {
-              asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(E.y) * (float)x[i])
-                           : "memory");
-            }
+        for (int i = 0; i < 8; ++i)
+          if (i < 4 * ni && da[i] >= 0) red(row + (uint32_t)da[i], E.y, x[i]);
+      }
+    };
+    // 32 postings of the packed short segments: one posting per lane, its
+    // own term and entries
+    auto score_packed = [&](int it) {
+      const int P = (it - total) * 32 + lane;
+      if (P >= tiny_total) return;
+      int jj = chunk_j0[it - total];
+      while (P >= s_tp[jj + 1]) ++jj;
+      const int rel = P - s_tp[jj] + s_off[jj];
+      const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
+      const int li = rel & 31;
+      const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
+      const uint32_t da = (uint32_t)(doc - doc0) * 4u;
+      AccT xv;
+      if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
+      else xv = (AccT)load_x<IMPACT>(blk, li);
+      const int32_t eb = s_e0[jj], ee = s_e1[jj];
+      for (int32_t en = eb; en < ee; ++en) {
+        const uint2 E = entry(en);
+        red(acc_s + E.x + da, E.y, xv);
+      }
+    };
+    // units are claimed two at a time; both items' postings are loaded
+    // before either is scored, so that each warp keeps 256 postings in flight
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&s_next, 2);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    while (nxt < units) {
+      const int it = nxt;
+      if (lane == 0) nxt = atomicAdd(&s_next, 2);
+      nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      if (it + 1 < total) {
+        int da[8];
+        AccT x[8];
+        const int ja = load_item(it, da, x);
+        const int jb = load_item(it + 1, da + 4, x + 4);
+        if (ja == jb) {
+          score_items(ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
+        } else {
+          score_items(ja, da, x, 1);
+          score_items(jb, da + 4, x + 4, 1);
+        }
+      } else {
+        for (int u = it; u < min(it + 2, units); ++u) {
+          if (u < total) {
+            int da[4];
+            AccT x[4];
+            const int jj = load_item(u, da, x);
+            score_items(jj, da, x, 1);
+          } else {
+            score_packed(u);
           }
         }
       }
