@@ -573,79 +573,82 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     return;
   }
   // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
-  // whole query rows: it counts the row's candidates, reserves the row's
-  // slots with one global atomic, then writes them; no block barrier.
+  // whole query rows and walks them in windows of 1024 documents: lane l
+  // compares documents 128 c + 4 l .. + 3 of chunk c = 0..7 and keeps one bit
+  // per document in two masks (above theta_q, equal to theta_q); one warp
+  // scan and one global atomic per window reserve the candidate slots, and
+  // each lane writes its own candidates.  No block barrier.
+  const int64_t n_in = N - doc0;  // documents of this tile inside the collection
   for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
     const int q = q0 + ql;
     const uint32_t th = s_theta[ql];
     const AccT* row = acc + ql * T;
-    auto masks = [&](int d0, uint4& raw, unsigned& gtm, unsigned& eqm) {
-      raw = *reinterpret_cast<const uint4*>(row + d0);
-      const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-      gtm = 0;
-      eqm = 0;
+    for (int w0 = 0; w0 < T; w0 += 1024) {
+      uint32_t gt_bits = 0, eq_bits = 0;
+      const int nc = min(8, (T - w0) / 128);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const bool in = doc0 + d0 + i < N;
-        bool gt, eq;
-        if (R <= 0) {
-          gt = in;
-          eq = false;
-        } else if (IMPACT == GS_IMPACT_U8) {
-          gt = in && (int32_t)rv[i] > (int32_t)th;
-          eq = in && (int32_t)rv[i] == (int32_t)th;
-        } else {
-          gt = in && __uint_as_float(rv[i]) > __uint_as_float(th);
-          eq = in && __uint_as_float(rv[i]) == __uint_as_float(th);
+      for (int c = 0; c < 8; ++c) {
+        if (c >= nc) break;
+        const int d0 = w0 + c * 128 + lane * 4;
+        const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
+        const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          bool gt, eq;
+          if (R <= 0) {
+            gt = true;
+            eq = false;
+          } else if (IMPACT == GS_IMPACT_U8) {
+            gt = (int32_t)rv[i] > (int32_t)th;
+            eq = (int32_t)rv[i] == (int32_t)th;
+          } else {
+            gt = __uint_as_float(rv[i]) > __uint_as_float(th);
+            eq = __uint_as_float(rv[i]) == __uint_as_float(th);
+          }
+          gt_bits |= (uint32_t)gt << (4 * c + i);
+          eq_bits |= (uint32_t)eq << (4 * c + i);
         }
-        gtm |= (unsigned)gt << i;
-        eqm |= (unsigned)eq << i;
       }
-    };
-    // pass 1: candidates of the row, and which 128-document chunks need pass 2
-    unsigned cnt = 0;
-    uint64_t chunk_hits = 0;
-    for (int c = 0; c < cpr; ++c) {
-      uint4 raw;
-      unsigned gtm, eqm;
-      masks(c * 128 + lane * 4, raw, gtm, eqm);
-      cnt += (unsigned)__popc(gtm);
-      if (__any_sync(0xffffffffu, (gtm | eqm) != 0)) chunk_hits |= 1ull << c;
-    }
-    const unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
-    uint32_t base = 0;
-    if (lane == 0 && tot) base = atomicAdd(&cand_cnt[q], tot);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    // pass 2: tie words and candidate writes, chunks with hits only
-    for (int c = 0; c < cpr; ++c) {
-      if (!(chunk_hits & (1ull << c))) continue;
-      const int d0 = c * 128 + lane * 4;
-      uint4 raw;
-      unsigned gtm, eqm;
-      masks(d0, raw, gtm, eqm);
-      unsigned word = eqm << (4 * (lane & 7));
-      word |= __shfl_xor_sync(0xffffffffu, word, 1);
-      word |= __shfl_xor_sync(0xffffffffu, word, 2);
-      word |= __shfl_xor_sync(0xffffffffu, word, 4);
-      const int64_t wdoc = doc0 + (d0 - (lane & 7) * 4);
-      if ((lane & 7) == 0 && word && wdoc < N) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
-      const int n_gt = __popc(gtm);
+      if (n_in < (int64_t)(w0 + 1024)) {
+        // the collection ends inside this window: drop documents >= N
+        uint32_t keep = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
+        gt_bits &= keep;
+        eq_bits &= keep;
+      }
+      const int n_gt = __popc(gt_bits);
       int incl = n_gt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      uint32_t slot = base + (uint32_t)(incl - n_gt);
-      base += (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
-      const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (gtm & (1u << i)) {
-          AccT v;
-          memcpy(&v, &rv[i], 4);
-          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(v), (uint32_t)(doc0 + d0 + i));
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (tot > 0) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        uint32_t slot = base + (uint32_t)(incl - n_gt);
+        while (gt_bits) {
+          const int bit = __ffs(gt_bits) - 1;
+          gt_bits &= gt_bits - 1;
+          const int d = w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3);
+          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(row[d]), (uint32_t)(doc0 + d));
           ++slot;
+        }
+      }
+      if (__any_sync(0xffffffffu, eq_bits != 0)) {
+        // tie words: 32 documents = 8 lanes x 4 bits of one chunk
+        for (int c = 0; c < nc; ++c) {
+          uint32_t word = ((eq_bits >> (4 * c)) & 15u) << (4 * (lane & 7));
+          word |= __shfl_xor_sync(0xffffffffu, word, 1);
+          word |= __shfl_xor_sync(0xffffffffu, word, 2);
+          word |= __shfl_xor_sync(0xffffffffu, word, 4);
+          const int64_t wdoc = doc0 + w0 + c * 128 + (lane >> 3) * 32;
+          if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
         }
       }
     }
