@@ -260,7 +260,8 @@ typedef struct {
   int32_t chunk_blocks;  /* TERM_PARALLEL: blocks per work item */
   int64_t cand_capacity; /* DOC_TILED: candidate slots per query */
   int32_t head_terms;    /* DOC_TILED: dense head terms used (0: none) */
-  int32_t reserved0;
+  int32_t ctas_per_sm;   /* DOC_TILED: resident CTAs per SM of the scoring
+                            kernel (occupancy calculator) */
   int64_t reserved[3];
 } gs_plan_info;
 

@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kDtThreads = 512;                  // two CTAs per SM (64 registers each)
 constexpr int kDtMaxAccBytes = 64 * 1024;     // G x T accumulators
-constexpr int kEntCap = 1536;                // query entries staged in shared memory (12 KB)
+constexpr int kEntCap = 1280;                // query entries staged in shared memory (10 KB)
 constexpr int kItemCap = 4608;               // (term, 128-posting chunk) items per term batch (9 KB)
 constexpr int kTinySeg = 64;                 // segments shorter than this are packed, not itemised
 constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting chunks per term batch
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     int64_t sample_docs, const uint32_t* __restrict__ theta, int k, uint2* __restrict__ cand,
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
     const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
-    const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact) {
+    const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
   // dynamic shared memory: [G x T accumulators][staged query entries][item -> term]
@@ -284,31 +284,24 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ __align__(16) AccT s_w[HEAD ? GS_MAX_HEAD_TERMS * kHeadG : 4];
   __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
+  __shared__ int32_t s_t[kDtThreads];   // the group's first terms
+  __shared__ int64_t s_tb[kDtThreads];  // and their first index blocks
+
+  // the CTA scores tiles [tile_begin, tile_end) of query group g; the
+  // group's data are read once and serve all of them
   const int g = blockIdx.x % ng;
-  const int tile_idx = blockIdx.x / ng;
-  int tau;
-  if (MODE == kModeSample) {
-    tau = tile_idx * R;
-  } else {
-    tau = tile_idx;
-    if (R > 0 && (tau % R) == 0 && tau / R < n_sample) return;  // a sample tile: already scored
-  }
+  const int tile_begin = (blockIdx.x / ng) * tiles_per_cta;
+  const int tile_end = min(tile_begin + tiles_per_cta, n_tiles);
   const int q0 = g * G;
   const int gq = min(G, B - q0);
-  const int64_t doc0 = (int64_t)tau * T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  {
-    uint4* a4 = reinterpret_cast<uint4*>(acc);
-    for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
-  }
   if (MODE == kModeMain)
     for (int i = threadIdx.x; i < gq; i += blockDim.x) s_theta[i] = R > 0 ? __ldg(theta + q0 + i) : 0u;
   const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
   const int nterm = n_u[g];
   const int32_t* ut = u_terms + ebase;
   const int32_t* up = u_ptr + ebase + g;
-  const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
   // the group's (query, weight) entries, staged with the query's row byte offset
   const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
   const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
@@ -320,10 +313,16 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       ent_s[i] = make_uint2(E.x * row_bytes, E.y);
     }
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  // terms per batch: their 128-posting work items must fit the item table
+  const int items_per_term = T / 128 + 1;
+  const int tb = min(kDtThreads, kItemCap / items_per_term);
+  if ((int)threadIdx.x < tb && (int)threadIdx.x < nterm) {
+    const int32_t t = ut[threadIdx.x];
+    s_t[threadIdx.x] = t;
+    s_tb[threadIdx.x] = __ldg(term_block + t);
+  }
   int nact = 0;
   if (HEAD) {
-    // head rows and weights of the group; the tile's head rows are prefetched
-    // into L2 now so that they are resident when the head phase reads them
     nact = head_nact[g];
     for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
     __syncthreads();
@@ -331,324 +330,343 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
       memcpy(&s_w[i], &raw, 4);
     }
-    const int ib = impact_bytes(IMPACT);
-    const int lines_per_row = (T * ib + 127) / 128;
-    for (int i = threadIdx.x; i < nact * lines_per_row; i += blockDim.x) {
-      const uint8_t* ptr = head_dense + ((int64_t)s_hact[i / lines_per_row] * head_ld + doc0) * ib +
-                           (int64_t)(i % lines_per_row) * 128;
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-    }
   }
-  // terms per batch: their 128-posting work items must fit the item table
-  const int items_per_term = T / 128 + 1;
-  const int tb = min(kDtThreads, kItemCap / items_per_term);
-  __syncthreads();
 
-  for (int j0 = 0; j0 < nterm; j0 += tb) {
-    const int j = j0 + threadIdx.x;
-    int items = 0, tiny = 0;
-    if (threadIdx.x < tb && j < nterm) {
-      const int32_t t = ut[j];
-      const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
-      const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
-      s_p0[threadIdx.x] = blocks + (__ldg(term_block + t) + (int64_t)(s >> 5)) * bb;
-      s_off[threadIdx.x] = (int32_t)(s & 31u);
-      s_len[threadIdx.x] = (int32_t)(e - s);
-      s_e0[threadIdx.x] = __ldg(up + j);
-      s_e1[threadIdx.x] = __ldg(up + j + 1);
-      if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
-      else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
+  for (int tile_idx = tile_begin; tile_idx < tile_end; ++tile_idx) {
+    int tau;
+    if (MODE == kModeSample) {
+      tau = tile_idx * R;
+    } else {
+      tau = tile_idx;
+      if (R > 0 && (tau % R) == 0 && tau / R < n_sample) continue;  // a sample tile: already scored
     }
-    int total, tiny_total;
-    const int xi = block_excl_scan(items, warp_buf, &total);
-    const int xt = block_excl_scan(tiny, warp_buf, &tiny_total);
-    if (threadIdx.x < tb) {
-      s_item[threadIdx.x] = xi;
-      s_tp[threadIdx.x] = xt;
+    const int64_t doc0 = (int64_t)tau * T;
+    const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
+    __syncthreads();  // the previous tile's rows are no longer read
+    {
+      uint4* a4 = reinterpret_cast<uint4*>(acc);
+      for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
     }
-    if (threadIdx.x == 0) s_tp[tb] = tiny_total;
-    for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
-    // packed chunk c starts inside the short segment that holds posting 32 c
-    for (int c = (xt + 31) / 32; 32 * c < xt + tiny; ++c) chunk_j0[c] = (uint16_t)threadIdx.x;
-    const int packed = (tiny_total + 31) / 32;
-    if (threadIdx.x == 0) s_next = 0;
+    if (HEAD) {
+      // the tile's head rows are prefetched into L2 now so that they are
+      // resident when the head phase reads them
+      const int ib = impact_bytes(IMPACT);
+      const int lines_per_row = (T * ib + 127) / 128;
+      for (int i = threadIdx.x; i < nact * lines_per_row; i += blockDim.x) {
+        const uint8_t* ptr = head_dense + ((int64_t)s_hact[i / lines_per_row] * head_ld + doc0) * ib +
+                             (int64_t)(i % lines_per_row) * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+      }
+    }
     __syncthreads();
-    const int units = total + packed;
-    // one (query, weight) entry of the group
-    auto entry = [&](int32_t en) {
-      uint2 E;
-      if (staged) {
-        E = ent_s[en - ent_lo];
-      } else {
-        E = __ldg(ent + en);
-        E.x *= row_bytes;
+
+    for (int j0 = 0; j0 < nterm; j0 += tb) {
+      const int j = j0 + threadIdx.x;
+      int items = 0, tiny = 0;
+      if (threadIdx.x < tb && j < nterm) {
+        const int32_t t = j0 == 0 ? s_t[threadIdx.x] : ut[j];
+        const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
+        const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
+        const int64_t tblk = j0 == 0 ? s_tb[threadIdx.x] : __ldg(term_block + t);
+        s_p0[threadIdx.x] = blocks + (tblk + (int64_t)(s >> 5)) * bb;
+        s_off[threadIdx.x] = (int32_t)(s & 31u);
+        s_len[threadIdx.x] = (int32_t)(e - s);
+        s_e0[threadIdx.x] = __ldg(up + j);
+        s_e1[threadIdx.x] = __ldg(up + j + 1);
+        if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
+        else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
       }
-      return E;
-    };
-    auto red = [&](uint32_t addr, uint32_t wbits, AccT xv) {
-      if (IMPACT == GS_IMPACT_U8)
-        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
-      else
-        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
-    };
-    // item it: lane l loads posting l of each of its 4 blocks; da = byte
-    // offset of the document inside a row, -1 when the lane has no posting
-    auto load_item = [&](int it, int* da, AccT* x) -> int {
-      const int jj = item_term[it];
-      const int c = it - s_item[jj];
-      const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
-      const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
-      const uint32_t len = (uint32_t)s_len[jj];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        da[i] = -1;
-        x[i] = (AccT)0;
-        if ((uint32_t)(rel + 32 * i) < len) {
-          const uint8_t* blk = base + i * bb;
-          const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
-          da[i] = (int)(doc - doc0) * 4;
-          if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
-          else x[i] = (AccT)load_x<IMPACT>(blk, lane);
-        }
+      int total, tiny_total;
+      const int xi = block_excl_scan(items, warp_buf, &total);
+      const int xt = block_excl_scan(tiny, warp_buf, &tiny_total);
+      if (threadIdx.x < tb) {
+        s_item[threadIdx.x] = xi;
+        s_tp[threadIdx.x] = xt;
       }
-      return jj;
-    };
-    // NI loaded items of term jj: every entry of the term, every posting
-    auto score_items = [&](int jj, const int* da, const AccT* x, int ni) {
-      const int32_t eb = s_e0[jj], ee = s_e1[jj];
-      for (int32_t en = eb; en < ee; ++en) {
-        const uint2 E = entry(en);
-        const uint32_t row = acc_s + E.x;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (i < 4 * ni && da[i] >= 0) red(row + (uint32_t)da[i], E.y, x[i]);
-      }
-    };
-    // 32 postings of the packed short segments: one posting per lane, its
-    // own term and entries
-    auto score_packed = [&](int it) {
-      const int P = (it - total) * 32 + lane;
-      if (P >= tiny_total) return;
-      int jj = chunk_j0[it - total];
-      while (P >= s_tp[jj + 1]) ++jj;
-      const int rel = P - s_tp[jj] + s_off[jj];
-      const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
-      const int li = rel & 31;
-      const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
-      const uint32_t da = (uint32_t)(doc - doc0) * 4u;
-      AccT xv;
-      if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
-      else xv = (AccT)load_x<IMPACT>(blk, li);
-      const int32_t eb = s_e0[jj], ee = s_e1[jj];
-      for (int32_t en = eb; en < ee; ++en) {
-        const uint2 E = entry(en);
-        red(acc_s + E.x + da, E.y, xv);
-      }
-    };
-    // units are claimed two at a time; both items' postings are loaded
-    // before either is scored, so that each warp keeps 256 postings in flight
-    int nxt = 0;
-    if (lane == 0) nxt = atomicAdd(&s_next, 2);
-    nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    while (nxt < units) {
-      const int it = nxt;
-      if (lane == 0) nxt = atomicAdd(&s_next, 2);
-      nxt = __shfl_sync(0xffffffffu, nxt, 0);
-      if (it + 1 < total) {
-        int da[8];
-        AccT x[8];
-        const int ja = load_item(it, da, x);
-        const int jb = load_item(it + 1, da + 4, x + 4);
-        if (ja == jb) {
-          score_items(ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
+      if (threadIdx.x == 0) s_tp[tb] = tiny_total;
+      for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
+      // packed chunk c starts inside the short segment that holds posting 32 c
+      for (int c = (xt + 31) / 32; 32 * c < xt + tiny; ++c) chunk_j0[c] = (uint16_t)threadIdx.x;
+      const int packed = (tiny_total + 31) / 32;
+      if (threadIdx.x == 0) s_next = 0;
+      __syncthreads();
+      const int units = total + packed;
+      // one (query, weight) entry of the group
+      auto entry = [&](int32_t en) {
+        uint2 E;
+        if (staged) {
+          E = ent_s[en - ent_lo];
         } else {
-          score_items(ja, da, x, 1);
-          score_items(jb, da + 4, x + 4, 1);
+          E = __ldg(ent + en);
+          E.x *= row_bytes;
         }
-      } else {
-        for (int u = it; u < min(it + 2, units); ++u) {
-          if (u < total) {
-            int da[4];
-            AccT x[4];
-            const int jj = load_item(u, da, x);
-            score_items(jj, da, x, 1);
-          } else {
-            score_packed(u);
+        return E;
+      };
+      auto red = [&](uint32_t addr, uint32_t wbits, AccT xv) {
+        if (IMPACT == GS_IMPACT_U8)
+          asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
+        else
+          asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
+      };
+      // item it: lane l loads posting l of each of its 4 blocks; da = byte
+      // offset of the document inside a row, -1 when the lane has no posting
+      auto load_item = [&](int it, int* da, AccT* x) -> int {
+        const int jj = item_term[it];
+        const int c = it - s_item[jj];
+        const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
+        const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
+        const uint32_t len = (uint32_t)s_len[jj];
+  #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          da[i] = -1;
+          x[i] = (AccT)0;
+          if ((uint32_t)(rel + 32 * i) < len) {
+            const uint8_t* blk = base + i * bb;
+            const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
+            da[i] = (int)(doc - doc0) * 4;
+            if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
+            else x[i] = (AccT)load_x<IMPACT>(blk, lane);
           }
         }
-      }
-    }
-    __syncthreads();
-  }
-
-  if (HEAD) {
-    // dense head: S[q][d] += sum_h W[q][h] * X[h][d].  Thread (warp w, lane
-    // l) owns queries 16 (w % 2) .. + 15 and documents 2 p, 2 p + 1 of each
-    // 1024-document slab, p = 32 (w / 2) + l: the head rows are read
-    // coalesced, four rows in flight, the weights are warp-wide broadcasts,
-    // and every (query, document) cell has one owner (no atomics).
-    // kHeadG / 16 warps share a document pair range; one slab = kSlab documents
-    constexpr int kQH = kHeadG / 16;
-    constexpr int kSlab = 2 * kDtThreads / kQH;
-    const int qh = warp % kQH;
-    const int dp = (warp / kQH) * 32 + lane;
-    for (int slab = 0; slab < T; slab += kSlab) {
-      if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
-      const int64_t col = doc0 + slab + 2 * dp;
-      AccT r[16][2];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
-      auto load2 = [&](int a, AccT& x0, AccT& x1) {
-        const int64_t at = (int64_t)s_hact[a] * head_ld + col;
-        if (IMPACT == GS_IMPACT_F32) {
-          const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
-          x0 = u.x;
-          x1 = u.y;
-        } else if (IMPACT == GS_IMPACT_U8) {
-          const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
-          x0 = (AccT)(u & 0xffu);
-          x1 = (AccT)(u >> 8);
-        } else {
-          const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
-          float2 f;
-          if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
-          else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
-          x0 = (AccT)f.x;
-          x1 = (AccT)f.y;
+        return jj;
+      };
+      // NI loaded items of term jj: every entry of the term, every posting
+      auto score_items = [&](int jj, const int* da, const AccT* x, int ni) {
+        const int32_t eb = s_e0[jj], ee = s_e1[jj];
+        for (int32_t en = eb; en < ee; ++en) {
+          const uint2 E = entry(en);
+          const uint32_t row = acc_s + E.x;
+  #pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (i < 4 * ni && da[i] >= 0) red(row + (uint32_t)da[i], E.y, x[i]);
         }
       };
-      for (int a0 = 0; a0 < nact; a0 += 4) {
-        AccT xs[4][2];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          xs[u][0] = xs[u][1] = (AccT)0;
-          if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+      // 32 postings of the packed short segments: one posting per lane, its
+      // own term and entries
+      auto score_packed = [&](int it) {
+        const int P = (it - total) * 32 + lane;
+        if (P >= tiny_total) return;
+        int jj = chunk_j0[it - total];
+        while (P >= s_tp[jj + 1]) ++jj;
+        const int rel = P - s_tp[jj] + s_off[jj];
+        const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
+        const int li = rel & 31;
+        const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
+        const uint32_t da = (uint32_t)(doc - doc0) * 4u;
+        AccT xv;
+        if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
+        else xv = (AccT)load_x<IMPACT>(blk, li);
+        const int32_t eb = s_e0[jj], ee = s_e1[jj];
+        for (int32_t en = eb; en < ee; ++en) {
+          const uint2 E = entry(en);
+          red(acc_s + E.x + da, E.y, xv);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (a0 + u >= nact) break;
-          const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
-#pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4) {
-            AccT w4[4];
-            *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              if (IMPACT == GS_IMPACT_U8) {
-                r[4 * q4 + v][0] += w4[v] * xs[u][0];
-                r[4 * q4 + v][1] += w4[v] * xs[u][1];
-              } else {
-                r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
-                r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
-              }
+      };
+      // units are claimed two at a time; both items' postings are loaded
+      // before either is scored, so that each warp keeps 256 postings in flight
+      int nxt = 0;
+      if (lane == 0) nxt = atomicAdd(&s_next, 2);
+      nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      while (nxt < units) {
+        const int it = nxt;
+        if (lane == 0) nxt = atomicAdd(&s_next, 2);
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        if (it + 1 < total) {
+          int da[8];
+          AccT x[8];
+          const int ja = load_item(it, da, x);
+          const int jb = load_item(it + 1, da + 4, x + 4);
+          if (ja == jb) {
+            score_items(ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
+          } else {
+            score_items(ja, da, x, 1);
+            score_items(jb, da + 4, x + 4, 1);
+          }
+        } else {
+          for (int u = it; u < min(it + 2, units); ++u) {
+            if (u < total) {
+              int da[4];
+              AccT x[4];
+              const int jj = load_item(u, da, x);
+              score_items(jj, da, x, 1);
+            } else {
+              score_packed(u);
             }
           }
         }
       }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int q = 16 * qh + i;
-        if (q < gq) {
-          AccT* dst = acc + q * T + slab + 2 * dp;
-          uint2 c = *reinterpret_cast<uint2*>(dst);
-          AccT* v = reinterpret_cast<AccT*>(&c);
-          v[0] += r[i][0];
-          v[1] += r[i][1];
-          *reinterpret_cast<uint2*>(dst) = c;
-        }
-      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
 
-  // epilogue: each warp step covers 128 documents of one query row (4 per lane)
-  const int cpr = T / 128;  // chunks per row
-  if (MODE == kModeSample) {
-    for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
-      const int ql = ci / cpr;
-      const int d0 = (ci - ql * cpr) * 128 + lane * 4;
-      *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
-          *reinterpret_cast<const uint4*>(acc + ql * T + d0);
-    }
-    return;
-  }
-  // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
-  // whole query rows and walks them in windows of 1024 documents: lane l
-  // compares documents 128 c + 4 l .. + 3 of chunk c = 0..7 and keeps one bit
-  // per document in two masks (above theta_q, equal to theta_q); one warp
-  // scan and one global atomic per window reserve the candidate slots, and
-  // each lane writes its own candidates.  No block barrier.
-  const int64_t n_in = N - doc0;  // documents of this tile inside the collection
-  for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
-    const int q = q0 + ql;
-    const uint32_t th = s_theta[ql];
-    const AccT* row = acc + ql * T;
-    for (int w0 = 0; w0 < T; w0 += 1024) {
-      uint32_t gt_bits = 0, eq_bits = 0;
-      const int nc = min(8, (T - w0) / 128);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c >= nc) break;
-        const int d0 = w0 + c * 128 + lane * 4;
-        const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
-        const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          bool gt, eq;
-          if (R <= 0) {
-            gt = true;
-            eq = false;
+    if (HEAD) {
+      // dense head: S[q][d] += sum_h W[q][h] * X[h][d].  Thread (warp w, lane
+      // l) owns queries 16 (w % 2) .. + 15 and documents 2 p, 2 p + 1 of each
+      // 1024-document slab, p = 32 (w / 2) + l: the head rows are read
+      // coalesced, four rows in flight, the weights are warp-wide broadcasts,
+      // and every (query, document) cell has one owner (no atomics).
+      // kHeadG / 16 warps share a document pair range; one slab = kSlab documents
+      constexpr int kQH = kHeadG / 16;
+      constexpr int kSlab = 2 * kDtThreads / kQH;
+      const int qh = warp % kQH;
+      const int dp = (warp / kQH) * 32 + lane;
+      for (int slab = 0; slab < T; slab += kSlab) {
+        if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
+        const int64_t col = doc0 + slab + 2 * dp;
+        AccT r[16][2];
+  #pragma unroll
+        for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
+        auto load2 = [&](int a, AccT& x0, AccT& x1) {
+          const int64_t at = (int64_t)s_hact[a] * head_ld + col;
+          if (IMPACT == GS_IMPACT_F32) {
+            const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
+            x0 = u.x;
+            x1 = u.y;
           } else if (IMPACT == GS_IMPACT_U8) {
-            gt = (int32_t)rv[i] > (int32_t)th;
-            eq = (int32_t)rv[i] == (int32_t)th;
+            const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
+            x0 = (AccT)(u & 0xffu);
+            x1 = (AccT)(u >> 8);
           } else {
-            gt = __uint_as_float(rv[i]) > __uint_as_float(th);
-            eq = __uint_as_float(rv[i]) == __uint_as_float(th);
+            const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
+            float2 f;
+            if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+            x0 = (AccT)f.x;
+            x1 = (AccT)f.y;
           }
-          gt_bits |= (uint32_t)gt << (4 * c + i);
-          eq_bits |= (uint32_t)eq << (4 * c + i);
+        };
+        for (int a0 = 0; a0 < nact; a0 += 4) {
+          AccT xs[4][2];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            xs[u][0] = xs[u][1] = (AccT)0;
+            if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+          }
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (a0 + u >= nact) break;
+            const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
+  #pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+              AccT w4[4];
+              *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+  #pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                if (IMPACT == GS_IMPACT_U8) {
+                  r[4 * q4 + v][0] += w4[v] * xs[u][0];
+                  r[4 * q4 + v][1] += w4[v] * xs[u][1];
+                } else {
+                  r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
+                  r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+                }
+              }
+            }
+          }
+        }
+  #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int q = 16 * qh + i;
+          if (q < gq) {
+            AccT* dst = acc + q * T + slab + 2 * dp;
+            uint2 c = *reinterpret_cast<uint2*>(dst);
+            AccT* v = reinterpret_cast<AccT*>(&c);
+            v[0] += r[i][0];
+            v[1] += r[i][1];
+            *reinterpret_cast<uint2*>(dst) = c;
+          }
         }
       }
-      if (n_in < (int64_t)(w0 + 1024)) {
-        // the collection ends inside this window: drop documents >= N
-        uint32_t keep = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
-        gt_bits &= keep;
-        eq_bits &= keep;
+      __syncthreads();
+    }
+
+    // epilogue: each warp step covers 128 documents of one query row (4 per lane)
+    const int cpr = T / 128;  // chunks per row
+    if (MODE == kModeSample) {
+      for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
+        const int ql = ci / cpr;
+        const int d0 = (ci - ql * cpr) * 128 + lane * 4;
+        *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
+            *reinterpret_cast<const uint4*>(acc + ql * T + d0);
       }
-      const int n_gt = __popc(gt_bits);
-      int incl = n_gt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      if (tot > 0) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        uint32_t slot = base + (uint32_t)(incl - n_gt);
-        while (gt_bits) {
-          const int bit = __ffs(gt_bits) - 1;
-          gt_bits &= gt_bits - 1;
-          const int d = w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3);
-          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(row[d]), (uint32_t)(doc0 + d));
-          ++slot;
+      continue;
+    }
+    // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
+    // whole query rows and walks them in windows of 1024 documents: lane l
+    // compares documents 128 c + 4 l .. + 3 of chunk c = 0..7 and keeps one bit
+    // per document in two masks (above theta_q, equal to theta_q); one warp
+    // scan and one global atomic per window reserve the candidate slots, and
+    // each lane writes its own candidates.  No block barrier.
+    const int64_t n_in = N - doc0;  // documents of this tile inside the collection
+    for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
+      const int q = q0 + ql;
+      const uint32_t th = s_theta[ql];
+      const AccT* row = acc + ql * T;
+      for (int w0 = 0; w0 < T; w0 += 1024) {
+        uint32_t gt_bits = 0, eq_bits = 0;
+        const int nc = min(8, (T - w0) / 128);
+  #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (c >= nc) break;
+          const int d0 = w0 + c * 128 + lane * 4;
+          const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
+          const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+  #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            bool gt, eq;
+            if (R <= 0) {
+              gt = true;
+              eq = false;
+            } else if (IMPACT == GS_IMPACT_U8) {
+              gt = (int32_t)rv[i] > (int32_t)th;
+              eq = (int32_t)rv[i] == (int32_t)th;
+            } else {
+              gt = __uint_as_float(rv[i]) > __uint_as_float(th);
+              eq = __uint_as_float(rv[i]) == __uint_as_float(th);
+            }
+            gt_bits |= (uint32_t)gt << (4 * c + i);
+            eq_bits |= (uint32_t)eq << (4 * c + i);
+          }
         }
-      }
-      if (__any_sync(0xffffffffu, eq_bits != 0)) {
-        // tie words: 32 documents = 8 lanes x 4 bits of one chunk
-        for (int c = 0; c < nc; ++c) {
-          uint32_t word = ((eq_bits >> (4 * c)) & 15u) << (4 * (lane & 7));
-          word |= __shfl_xor_sync(0xffffffffu, word, 1);
-          word |= __shfl_xor_sync(0xffffffffu, word, 2);
-          word |= __shfl_xor_sync(0xffffffffu, word, 4);
-          const int64_t wdoc = doc0 + w0 + c * 128 + (lane >> 3) * 32;
-          if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+        if (n_in < (int64_t)(w0 + 1024)) {
+          // the collection ends inside this window: drop documents >= N
+          uint32_t keep = 0;
+  #pragma unroll
+          for (int c = 0; c < 8; ++c)
+  #pragma unroll
+            for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
+          gt_bits &= keep;
+          eq_bits &= keep;
+        }
+        const int n_gt = __popc(gt_bits);
+        int incl = n_gt;
+  #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot > 0) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          uint32_t slot = base + (uint32_t)(incl - n_gt);
+          while (gt_bits) {
+            const int bit = __ffs(gt_bits) - 1;
+            gt_bits &= gt_bits - 1;
+            const int d = w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3);
+            if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(row[d]), (uint32_t)(doc0 + d));
+            ++slot;
+          }
+        }
+        if (__any_sync(0xffffffffu, eq_bits != 0)) {
+          // tie words: 32 documents = 8 lanes x 4 bits of one chunk
+          for (int c = 0; c < nc; ++c) {
+            uint32_t word = ((eq_bits >> (4 * c)) & 15u) << (4 * (lane & 7));
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            word |= __shfl_xor_sync(0xffffffffu, word, 4);
+            const int64_t wdoc = doc0 + w0 + c * 128 + (lane >> 3) * 32;
+            if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+          }
         }
       }
     }
@@ -759,35 +777,60 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   }
 }
 
+constexpr size_t kDynSmemFixed = kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
+
+// Raises the dynamic shared-memory ceiling of both tile kernels of this
+// form, once per device: no attribute call is issued while a stream is
+// being captured for a graph.
+template <int IMPACT, bool HEAD>
+gs_status tile_smem_attr() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  GS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 128) return GS_ERR_UNSUPPORTED;
+  if (!done[dev]) {
+    const int ceil_bytes = (int)(kDtMaxAccBytes + kDynSmemFixed);
+    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeSample, HEAD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
+    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeMain, HEAD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
+    done[dev] = true;
+  }
+  return GS_OK;
+}
+
+template <int IMPACT, bool HEAD>
+gs_status tile_occupancy(const DtConfig& c, int* ctas) {
+  gs_status st = tile_smem_attr<IMPACT, HEAD>();
+  if (st != GS_OK) return st;
+  const size_t smem = (size_t)c.G * c.T * 4 + kDynSmemFixed;
+  GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, dt_tile_kernel<IMPACT, kModeMain, HEAD>,
+                                                            kDtThreads, smem));
+  return GS_OK;
+}
+
 template <int IMPACT, bool HEAD>
 gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
                          const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
-  const size_t smem =
-      (size_t)c.G * c.T * 4 + kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
+  const size_t smem = (size_t)c.G * c.T * 4 + kDynSmemFixed;
   auto ks = dt_tile_kernel<IMPACT, kModeSample, HEAD>;
   auto km = dt_tile_kernel<IMPACT, kModeMain, HEAD>;
-  // the dynamic shared-memory ceiling only grows, once per device: no
-  // attribute call is issued while a stream is being captured for a graph
-  static std::mutex mu;
-  static size_t set_for[128] = {};
-  {
-    int dev = 0;
-    GS_CUDA_TRY(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev < 0 || dev >= 128) return GS_ERR_UNSUPPORTED;
-    if (set_for[dev] < smem) {
-      const size_t ceil_bytes = (size_t)kDtMaxAccBytes + kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
-      GS_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ceil_bytes));
-      GS_CUDA_TRY(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ceil_bytes));
-      set_for[dev] = ceil_bytes;
-    }
-  }
+  gs_status st = tile_smem_attr<IMPACT, HEAD>();
+  if (st != GS_OK) return st;
+  // tiles per CTA: enough CTAs for at least 16 waves of resident CTAs
+  const int sms = ix->sms > 0 ? ix->sms : 1;
+  auto per_cta = [&](int n_tiles) {
+    const int64_t items = (int64_t)n_tiles * c.ng;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(8, items / (2 * (int64_t)sms * 16)));
+  };
   if (c.R > 0) {
-    ks<<<c.n_sample * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N,
-                                                   q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample,
-                                                   p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta,
-                                                   k, p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->head_dense,
-                                                   ix->head_ld, c.H, p.headw, p.head_act, p.head_nact);
+    const int ms = per_cta(c.n_sample);
+    ks<<<((c.n_sample + ms - 1) / ms) * c.ng, kDtThreads, smem, s>>>(
+        ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
+        c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
+        p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, ms, c.n_sample);
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
@@ -801,11 +844,11 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
     record_stage(opts, 2, s);
   }
   record_stage(opts, 3, s);
-  km<<<c.nt * c.ng, kDtThreads, smem, s>>>(ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B,
-                                           q_nnz, c.G, c.T, c.m, c.R, c.ng, c.n_sample, p.u_terms, p.u_ptr, p.n_u,
-                                           p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
-                                           p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act,
-                                           p.head_nact);
+  const int mm = per_cta(c.nt);
+  km<<<((c.nt + mm - 1) / mm) * c.ng, kDtThreads, smem, s>>>(
+      ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
+      c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
+      p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, mm, c.nt);
   GS_LAUNCH_CHECK();
   record_stage(opts, 4, s);
   return GS_OK;
@@ -833,6 +876,16 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
   out->sample_tiles = c.n_sample;
   out->cand_capacity = c.cap;
   out->head_terms = c.H;
+  int ctas = 0;
+  const bool head = c.H > 0;
+  switch (ix->impact) {
+    case GS_IMPACT_F32: st = head ? tile_occupancy<GS_IMPACT_F32, true>(c, &ctas) : tile_occupancy<GS_IMPACT_F32, false>(c, &ctas); break;
+    case GS_IMPACT_F16: st = head ? tile_occupancy<GS_IMPACT_F16, true>(c, &ctas) : tile_occupancy<GS_IMPACT_F16, false>(c, &ctas); break;
+    case GS_IMPACT_BF16: st = head ? tile_occupancy<GS_IMPACT_BF16, true>(c, &ctas) : tile_occupancy<GS_IMPACT_BF16, false>(c, &ctas); break;
+    default: st = head ? tile_occupancy<GS_IMPACT_U8, true>(c, &ctas) : tile_occupancy<GS_IMPACT_U8, false>(c, &ctas); break;
+  }
+  if (st != GS_OK) return st;
+  out->ctas_per_sm = ctas;
   return GS_OK;
 }
 

@@ -56,7 +56,7 @@ class gs_index_stats(ctypes.Structure):
                 ("blocks", ctypes.c_int64), ("posting_bytes", ctypes.c_int64), ("meta_bytes", ctypes.c_int64),
                 ("vocab", ctypes.c_int32), ("impact", ctypes.c_int32), ("block_bytes", ctypes.c_int32),
                 ("tile_docs", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("score_is_int", ctypes.c_int32),
-                ("head_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("head_bytes", ctypes.c_int64)]
+                ("head_terms", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("head_bytes", ctypes.c_int64)]
 
 
 class gs_index_layout(ctypes.Structure):
@@ -76,7 +76,7 @@ class gs_plan_info(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
                 ("sample_stride", ctypes.c_int32), ("num_groups", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("sample_tiles", ctypes.c_int32), ("chunk_blocks", ctypes.c_int32),
-                ("cand_capacity", ctypes.c_int64), ("head_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("cand_capacity", ctypes.c_int64), ("head_terms", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("reserved", ctypes.c_int64 * 3)]
 
 

@@ -133,6 +133,28 @@ def test_dense_head_layout(cases):
             assert np.array_equal(dense[h], row)
 
 
+@pytest.mark.parametrize("impact", ["f32", "f16", "bf16", "u8"])
+def test_doc_tiled_keeps_two_ctas_per_sm(impact):
+    """The scoring kernel's shared memory leaves room for two resident CTAs
+    per SM, with and without the dense head, for every tile shape the
+    autotuner tries."""
+    gs = _gs()
+    dev = _dev()
+    docs = synth.docs(20_000, seed=3)
+    idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                            torch.from_numpy(docs.weights).to(dev), docs.vocab, impact)
+    try:
+        for use_head in (1, -1):
+            for G, T in ((16, 1024), (8, 2048), (4, 4096)):
+                if use_head > 0 and G != 16:
+                    continue
+                plan = idx.plan(64, 64 * 30, 100, gs.make_opts("doc_tiled", group_queries=G, tile_docs=T,
+                                                               use_head=use_head))
+                assert plan.algo == 2 and plan.tile_docs == T
+                assert plan.ctas_per_sm == 2, (impact, use_head, G, T, plan.ctas_per_sm)
+    finally:
+        idx.free()
+
 @pytest.mark.parametrize("impact", ["f32", "u8"])
 def test_dense_rows_full_matrix(cases, impact):
     """Every score of the [B, N] matrix (gs_score_dense) against the oracle rows."""
