@@ -60,12 +60,10 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0 || c->T > 8192) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
-  // the dense head keeps one accumulator register per query of the group
-  // auto: the head pays off where shared-memory float reductions are slow;
-  // integer reductions (uint8 path) are cheap enough without it
+  // the dense head (tensor cores) serves groups of kHeadG queries; use_head
+  // < 0 turns it off
   const int use_head = opts ? opts->use_head : 0;
-  const bool head = ix->head_H > 0 && G == kHeadG &&
-                    (use_head > 0 || (use_head == 0 && ix->impact != GS_IMPACT_U8));
+  const bool head = ix->head_H > 0 && G == kHeadG && use_head >= 0;
   c->H = head ? ix->head_H : 0;
   G = head ? kHeadG : std::min(std::min(G, B), kMaxGroup);
   if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {
@@ -245,6 +243,28 @@ __device__ __forceinline__ uint32_t theta_key(const uint32_t* theta, int64_t q, 
   return score_key((int32_t)raw);
 }
 
+// TF32 operand: x rounded to 10 explicit mantissa bits (ties away from zero)
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// d += A B for one m16n8k8 tile (TF32 operands, FP32 accumulators)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// one stored impact as FP32 (exact)
+template <int IMPACT>
+__device__ __forceinline__ float load_impact(const uint8_t* p) {
+  if (IMPACT == GS_IMPACT_F32) return __ldg(reinterpret_cast<const float*>(p));
+  if (IMPACT == GS_IMPACT_F16) return __half2float(__ldg(reinterpret_cast<const __half*>(p)));
+  if (IMPACT == GS_IMPACT_BF16) return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p)));
+  return (float)__ldg(p);
+}
+
 // One CTA per (tile, group): G x T score block in shared memory.
 //
 // Work items are (term, chunk of 4 posting blocks = 128 postings) pairs of
@@ -281,11 +301,14 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
   __shared__ int s_next;
-  __shared__ __align__(16) AccT s_w[HEAD ? GS_MAX_HEAD_TERMS * kHeadG : 4];
+  // head weights: FP32 impacts W[a][q] (a < nact rows, q < 16 queries);
+  // others as m16n8k8 A fragments [k-step][lane] (high part, low part)
+  __shared__ uint4 s_af[HEAD ? (GS_MAX_HEAD_TERMS / 8) * 32 * 2 : 1];
+  float* s_w = reinterpret_cast<float*>(s_af);
+  __shared__ int s_tc;  // the head runs on the tensor cores
   __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
-  __shared__ int32_t s_t[kDtThreads];   // the group's first terms
-  __shared__ int64_t s_tb[kDtThreads];  // and their first index blocks
+  __shared__ int32_t s_t[kDtThreads];  // the group's first terms
 
   // the CTA scores tiles [tile_begin, tile_end) of query group g; the
   // group's data are read once and serve all of them
@@ -317,18 +340,46 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   const int items_per_term = T / 128 + 1;
   const int tb = min(kDtThreads, kItemCap / items_per_term);
   if ((int)threadIdx.x < tb && (int)threadIdx.x < nterm) {
-    const int32_t t = ut[threadIdx.x];
-    s_t[threadIdx.x] = t;
-    s_tb[threadIdx.x] = __ldg(term_block + t);
+    s_t[threadIdx.x] = ut[threadIdx.x];
   }
   int nact = 0;
   if (HEAD) {
     nact = head_nact[g];
     for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
     __syncthreads();
-    for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
-      const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
-      memcpy(&s_w[i], &raw, 4);
+    // FP32 impacts: W[a][q] for the FMA head.  Others: A fragments of
+    // W[q][a] (q < 16 queries, a < nact rows), k-step ks,
+    // lane (gid, tig): W[gid][8 ks + tig], W[gid + 8][...], W[gid][8 ks + tig + 4],
+    // W[gid + 8][...]; each weight w = high + low, both TF32.  uint8 weights
+    // are integers: exact in TF32 and summed exactly in FP32 while every
+    // partial sum stays below 2^24 (weights <= 1023, 255 per impact, <= 64 rows)
+    if (threadIdx.x == 0) s_tc = IMPACT != GS_IMPACT_F32;
+    __syncthreads();
+    if (IMPACT == GS_IMPACT_F32)
+      for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x)
+        s_w[i] = __uint_as_float(__ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG)));
+    const int KS = IMPACT == GS_IMPACT_F32 ? 0 : (nact + 7) / 8;
+    for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
+      const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int q = gid + 8 * (e & 1);
+        const int a = 8 * ks + tig + 4 * (e >> 1);
+        uint32_t raw = 0u;
+        if (a < nact) raw = __ldg(headw + ((int64_t)g * H + s_hact[a]) * kHeadG + q);
+        float w;
+        if (IMPACT == GS_IMPACT_U8) {
+          if ((int32_t)raw > 1023 || (int32_t)raw < 0) s_tc = 0;
+          w = (float)(int32_t)raw;
+        } else {
+          w = __uint_as_float(raw);
+        }
+        hi[e] = to_tf32(w);
+        lo[e] = to_tf32(w - __uint_as_float(hi[e]));
+      }
+      s_af[2 * i] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      s_af[2 * i + 1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
 
@@ -367,8 +418,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         const int32_t t = j0 == 0 ? s_t[threadIdx.x] : ut[j];
         const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
         const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
-        const int64_t tblk = j0 == 0 ? s_tb[threadIdx.x] : __ldg(term_block + t);
-        s_p0[threadIdx.x] = blocks + (tblk + (int64_t)(s >> 5)) * bb;
+        s_p0[threadIdx.x] = blocks + (__ldg(term_block + t) + (int64_t)(s >> 5)) * bb;
         s_off[threadIdx.x] = (int32_t)(s & 31u);
         s_len[threadIdx.x] = (int32_t)(e - s);
         s_e0[threadIdx.x] = __ldg(up + j);
@@ -499,79 +549,154 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     }
 
     if (HEAD) {
-      // dense head: S[q][d] += sum_h W[q][h] * X[h][d].  Thread (warp w, lane
-      // l) owns queries 16 (w % 2) .. + 15 and documents 2 p, 2 p + 1 of each
-      // 1024-document slab, p = 32 (w / 2) + l: the head rows are read
-      // coalesced, four rows in flight, the weights are warp-wide broadcasts,
-      // and every (query, document) cell has one owner (no atomics).
-      // kHeadG / 16 warps share a document pair range; one slab = kSlab documents
-      constexpr int kQH = kHeadG / 16;
-      constexpr int kSlab = 2 * kDtThreads / kQH;
-      const int qh = warp % kQH;
-      const int dp = (warp / kQH) * 32 + lane;
-      for (int slab = 0; slab < T; slab += kSlab) {
-        if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
-        const int64_t col = doc0 + slab + 2 * dp;
-        AccT r[16][2];
-  #pragma unroll
-        for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
-        auto load2 = [&](int a, AccT& x0, AccT& x1) {
-          const int64_t at = (int64_t)s_hact[a] * head_ld + col;
-          if (IMPACT == GS_IMPACT_F32) {
-            const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
-            x0 = u.x;
-            x1 = u.y;
-          } else if (IMPACT == GS_IMPACT_U8) {
-            const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
-            x0 = (AccT)(u & 0xffu);
-            x1 = (AccT)(u >> 8);
-          } else {
-            const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
-            float2 f;
-            if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
-            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
-            x0 = (AccT)f.x;
-            x1 = (AccT)f.y;
-          }
-        };
-        for (int a0 = 0; a0 < nact; a0 += 4) {
-          AccT xs[4][2];
-  #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            xs[u][0] = xs[u][1] = (AccT)0;
-            if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
-          }
-  #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (a0 + u >= nact) break;
-            const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
-  #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-              AccT w4[4];
-              *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
-  #pragma unroll
-              for (int v = 0; v < 4; ++v) {
-                if (IMPACT == GS_IMPACT_U8) {
-                  r[4 * q4 + v][0] += w4[v] * xs[u][0];
-                  r[4 * q4 + v][1] += w4[v] * xs[u][1];
-                } else {
-                  r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
-                  r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+      // dense head: S[q][d] += sum_a W[q][a] X[a][d] over the group's active
+      // head rows a, a contraction of 16 queries x nact rows x T documents.
+      const int ib = impact_bytes(IMPACT);
+      if (IMPACT == GS_IMPACT_F32) {
+        // FP32 impacts: FMAs.  Thread (warp w, lane l) owns the 16 queries and
+        // documents 2 p, 2 p + 1 of each 1024-document slab, p = 32 w + l:
+        // the head rows are read coalesced, four rows in flight, the weights
+        // are warp-wide broadcasts, and every (query, document) cell has one
+        // owner (no atomics)
+        constexpr int kSlab = 2 * kDtThreads;
+        const int dp = warp * 32 + lane;
+        for (int slab = 0; slab < T; slab += kSlab) {
+          if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
+          const int64_t col = doc0 + slab + 2 * dp;
+          float r[16][2];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0.f;
+          for (int a0 = 0; a0 < nact; a0 += 4) {
+            float2 xs[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              xs[u] = make_float2(0.f, 0.f);
+              if (a0 + u < nact)
+                xs[u] = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) +
+                                                              (int64_t)s_hact[a0 + u] * head_ld + col));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (a0 + u >= nact) break;
+              const float4* wr = reinterpret_cast<const float4*>(s_w + (a0 + u) * kHeadG);
+#pragma unroll
+              for (int q4 = 0; q4 < 4; ++q4) {
+                const float4 w4 = wr[q4];
+                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                  r[4 * q4 + v][0] = fmaf(wv[v], xs[u].x, r[4 * q4 + v][0]);
+                  r[4 * q4 + v][1] = fmaf(wv[v], xs[u].y, r[4 * q4 + v][1]);
                 }
               }
             }
           }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < gq) {
+              float2* dst = reinterpret_cast<float2*>(acc + i * T + slab + 2 * dp);
+              float2 c = *dst;
+              c.x += r[i][0];
+              c.y += r[i][1];
+              *dst = c;
+            }
+          }
         }
-  #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int q = 16 * qh + i;
-          if (q < gq) {
-            AccT* dst = acc + q * T + slab + 2 * dp;
-            uint2 c = *reinterpret_cast<uint2*>(dst);
-            AccT* v = reinterpret_cast<AccT*>(&c);
-            v[0] += r[i][0];
-            v[1] += r[i][1];
-            *reinterpret_cast<uint2*>(dst) = c;
+      } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
+        // FP16, BF16 and uint8 impacts: m16n8k8 TF32 MMAs on the tensor
+        // cores, M = the 16 queries, N = 8 documents, K = 8 rows.  Warp w
+        // owns documents [w T / 16, (w + 1) T / 16) and every (query,
+        // document) cell of them (no atomics).  The impacts are exact in
+        // TF32; W = high + low TF32 parts keeps FP32 accuracy (uint8 weights
+        // are exact integers and need the high part only)
+        const int gid = lane >> 2, tig = lane & 3;
+        const int KS = (nact + 7) / 8;
+        const int dpw = T / (kDtThreads / 32);  // documents per warp
+        const int ntiles = dpw / 8;
+        for (int n0 = 0; n0 < ntiles; n0 += 4) {
+          float d[4][4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
+          for (int ks = 0; ks < KS; ++ks) {
+            const uint4 ah = s_af[2 * (ks * 32 + lane)];
+            const uint4 al = s_af[2 * (ks * 32 + lane) + 1];
+            const uint32_t a_hi[4] = {ah.x, ah.y, ah.z, ah.w};
+            const uint32_t a_lo[4] = {al.x, al.y, al.z, al.w};
+            // B fragment rows 8 ks + tig and 8 ks + tig + 4, column gid of each 8-document tile
+            const int r0 = 8 * ks + tig, r1 = r0 + 4;
+            const int64_t col = doc0 + warp * dpw + n0 * 8 + gid;
+            const uint8_t* p0 = r0 < nact ? head_dense + ((int64_t)s_hact[r0] * head_ld + col) * ib : nullptr;
+            const uint8_t* p1 = r1 < nact ? head_dense + ((int64_t)s_hact[r1] * head_ld + col) * ib : nullptr;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (n0 + j >= ntiles) break;
+              float x0 = 0.f, x1 = 0.f;
+              if (p0) x0 = load_impact<IMPACT>(p0 + j * 8 * ib);
+              if (p1) x1 = load_impact<IMPACT>(p1 + j * 8 * ib);
+              if (IMPACT == GS_IMPACT_U8) {
+                mma_tf32(d[j], a_hi, __float_as_uint(x0), __float_as_uint(x1));
+              } else {
+                mma_tf32(d[j], a_lo, __float_as_uint(x0), __float_as_uint(x1));
+                mma_tf32(d[j], a_hi, __float_as_uint(x0), __float_as_uint(x1));
+              }
+            }
+          }
+          // D fragment: (query gid, documents 2 tig, 2 tig + 1) and (query gid + 8, same)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (n0 + j >= ntiles) break;
+            const int dc = warp * dpw + (n0 + j) * 8 + 2 * tig;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int q = gid + 8 * h;
+              if (q >= gq) continue;
+              if (IMPACT == GS_IMPACT_U8) {
+                int2* dst = reinterpret_cast<int2*>(acc + q * T + dc);
+                int2 c = *dst;
+                c.x += __float2int_rn(d[j][2 * h]);
+                c.y += __float2int_rn(d[j][2 * h + 1]);
+                *dst = c;
+              } else {
+                float2* dst = reinterpret_cast<float2*>(acc + q * T + dc);
+                float2 c = *dst;
+                c.x += d[j][2 * h];
+                c.y += d[j][2 * h + 1];
+                *dst = c;
+              }
+            }
+          }
+        }
+      } else {
+        // uint8 weights too large for exact FP32 sums: integer FMAs, thread
+        // (warp w, lane l) owns the 16 queries and documents 2 p, 2 p + 1 of
+        // each 1024-document slab, p = 32 w + l
+        for (int slab = 0; slab < T; slab += 2 * kDtThreads) {
+          const int dp = warp * 32 + lane;
+          if (slab + 2 * dp >= T) break;
+          const int64_t col = doc0 + slab + 2 * dp;
+          int32_t r[16][2];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0;
+          for (int a = 0; a < nact; ++a) {
+            const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(head_dense + (int64_t)s_hact[a] * head_ld + col));
+            const int32_t x0 = v & 0xff, x1 = v >> 8;
+            const uint32_t* wr = headw + ((int64_t)g * H + s_hact[a]) * kHeadG;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int32_t w = (int32_t)__ldg(wr + i);
+              r[i][0] += w * x0;
+              r[i][1] += w * x1;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < gq) {
+              int2* dst = reinterpret_cast<int2*>(acc + i * T + slab + 2 * dp);
+              int2 c = *dst;
+              c.x += r[i][0];
+              c.y += r[i][1];
+              *dst = c;
+            }
           }
         }
       }
