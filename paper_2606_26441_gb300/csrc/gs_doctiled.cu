@@ -265,6 +265,20 @@ __device__ __forceinline__ float load_impact(const uint8_t* p) {
   return (float)__ldg(p);
 }
 
+// element j (0..3) of four consecutive stored impacts, as TF32 operand bits
+// (exact: FP16, BF16 and uint8 values have at most 11 significant bits)
+template <int IMPACT, typename V>
+__device__ __forceinline__ uint32_t impact_tf32(V v, int j) {
+  if constexpr (IMPACT == GS_IMPACT_U8) {
+    return __float_as_uint((float)((v >> (8 * j)) & 0xffu));
+  } else {
+    const uint32_t w = j < 2 ? v.x : v.y;
+    const uint16_t hbits = (uint16_t)(j & 1 ? w >> 16 : w & 0xffffu);
+    if (IMPACT == GS_IMPACT_BF16) return (uint32_t)hbits << 16;
+    return __float_as_uint(__half2float(__ushort_as_half(hbits)));
+  }
+}
+
 // One CTA per (tile, group): G x T score block in shared memory.
 //
 // Work items are (term, chunk of 4 posting blocks = 128 postings) pairs of
@@ -604,64 +618,75 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         }
       } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
         // FP16, BF16 and uint8 impacts: m16n8k8 TF32 MMAs on the tensor
-        // cores, M = the 16 queries, N = 8 documents, K = 8 rows.  Warp w
-        // owns documents [w T / 16, (w + 1) T / 16) and every (query,
-        // document) cell of them (no atomics).  The impacts are exact in
-        // TF32; W = high + low TF32 parts keeps FP32 accuracy (uint8 weights
-        // are exact integers and need the high part only)
+        // cores, M = the 16 queries, K = 8 rows, N = 8 documents.  A warp
+        // step covers 32 documents base + 0..31 as four MMA tiles: column n
+        // of tile j is document base + 4 n + j, so that lane (gid, tig)
+        // reads documents base + 4 gid .. + 3 of a row with one vector load
+        // (its B operand for all four tiles) and owns documents
+        // base + 8 tig .. + 7 of queries gid, gid + 8 in the D fragments.
+        // Every (query, document) cell has one owner (no atomics).  The
+        // impacts are exact in TF32; W = high + low TF32 parts keeps FP32
+        // accuracy (uint8 weights are exact integers: high part only).
         const int gid = lane >> 2, tig = lane & 3;
         const int KS = (nact + 7) / 8;
-        const int dpw = T / (kDtThreads / 32);  // documents per warp
-        const int ntiles = dpw / 8;
-        for (int n0 = 0; n0 < ntiles; n0 += 4) {
+        constexpr int KB = 4;  // k-steps whose operands are loaded together
+        using VecT = typename std::conditional<IMPACT == GS_IMPACT_U8, uint32_t, uint2>::type;
+        for (int cb = warp * 32; cb < T; cb += kDtThreads) {
+          const int64_t col = doc0 + cb + 4 * gid;
           float d[4][4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
-          for (int ks = 0; ks < KS; ++ks) {
-            const uint4 ah = s_af[2 * (ks * 32 + lane)];
-            const uint4 al = s_af[2 * (ks * 32 + lane) + 1];
-            const uint32_t a_hi[4] = {ah.x, ah.y, ah.z, ah.w};
-            const uint32_t a_lo[4] = {al.x, al.y, al.z, al.w};
-            // B fragment rows 8 ks + tig and 8 ks + tig + 4, column gid of each 8-document tile
-            const int r0 = 8 * ks + tig, r1 = r0 + 4;
-            const int64_t col = doc0 + warp * dpw + n0 * 8 + gid;
-            const uint8_t* p0 = r0 < nact ? head_dense + ((int64_t)s_hact[r0] * head_ld + col) * ib : nullptr;
-            const uint8_t* p1 = r1 < nact ? head_dense + ((int64_t)s_hact[r1] * head_ld + col) * ib : nullptr;
+          for (int k0 = 0; k0 < KS; k0 += KB) {
+            VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, four documents each
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (n0 + j >= ntiles) break;
-              float x0 = 0.f, x1 = 0.f;
-              if (p0) x0 = load_impact<IMPACT>(p0 + j * 8 * ib);
-              if (p1) x1 = load_impact<IMPACT>(p1 + j * 8 * ib);
-              if (IMPACT == GS_IMPACT_U8) {
-                mma_tf32(d[j], a_hi, __float_as_uint(x0), __float_as_uint(x1));
-              } else {
-                mma_tf32(d[j], a_lo, __float_as_uint(x0), __float_as_uint(x1));
-                mma_tf32(d[j], a_hi, __float_as_uint(x0), __float_as_uint(x1));
+            for (int u = 0; u < KB; ++u)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int r = 8 * (k0 + u) + tig + 4 * h;
+                xv[u][h] = VecT{};
+                if (r < nact)
+                  xv[u][h] = __ldg(reinterpret_cast<const VecT*>(head_dense + ((int64_t)s_hact[r] * head_ld + col) * ib));
+              }
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+              if (k0 + u >= KS) break;
+              const uint4 ah = s_af[2 * ((k0 + u) * 32 + lane)];
+              const uint32_t a_hi[4] = {ah.x, ah.y, ah.z, ah.w};
+              uint32_t a_lo[4] = {0u, 0u, 0u, 0u};
+              if (IMPACT != GS_IMPACT_U8) {
+                const uint4 al = s_af[2 * ((k0 + u) * 32 + lane) + 1];
+                a_lo[0] = al.x; a_lo[1] = al.y; a_lo[2] = al.z; a_lo[3] = al.w;
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const uint32_t b0 = impact_tf32<IMPACT>(xv[u][0], j), b1 = impact_tf32<IMPACT>(xv[u][1], j);
+                if (IMPACT != GS_IMPACT_U8) mma_tf32(d[j], a_lo, b0, b1);
+                mma_tf32(d[j], a_hi, b0, b1);
               }
             }
           }
-          // D fragment: (query gid, documents 2 tig, 2 tig + 1) and (query gid + 8, same)
+          // D: (query gid + 8 h, documents cb + 8 tig + 4 c + j) = d[j][2 h + c]
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (n0 + j >= ntiles) break;
-            const int dc = warp * dpw + (n0 + j) * 8 + 2 * tig;
+          for (int h = 0; h < 2; ++h) {
+            const int q = gid + 8 * h;
+            if (q >= gq) continue;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int q = gid + 8 * h;
-              if (q >= gq) continue;
+            for (int c = 0; c < 2; ++c) {
+              AccT* dst = acc + q * T + cb + 8 * tig + 4 * c;
               if (IMPACT == GS_IMPACT_U8) {
-                int2* dst = reinterpret_cast<int2*>(acc + q * T + dc);
-                int2 c = *dst;
-                c.x += __float2int_rn(d[j][2 * h]);
-                c.y += __float2int_rn(d[j][2 * h + 1]);
-                *dst = c;
+                int4 v = *reinterpret_cast<int4*>(dst);
+                v.x += __float2int_rn(d[0][2 * h + c]);
+                v.y += __float2int_rn(d[1][2 * h + c]);
+                v.z += __float2int_rn(d[2][2 * h + c]);
+                v.w += __float2int_rn(d[3][2 * h + c]);
+                *reinterpret_cast<int4*>(dst) = v;
               } else {
-                float2* dst = reinterpret_cast<float2*>(acc + q * T + dc);
-                float2 c = *dst;
-                c.x += d[j][2 * h];
-                c.y += d[j][2 * h + 1];
-                *dst = c;
+                float4 v = *reinterpret_cast<float4*>(dst);
+                v.x += d[0][2 * h + c];
+                v.y += d[1][2 * h + c];
+                v.z += d[2][2 * h + c];
+                v.w += d[3][2 * h + c];
+                *reinterpret_cast<float4*>(dst) = v;
               }
             }
           }
