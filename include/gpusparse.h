@@ -172,9 +172,11 @@ typedef struct {
   int32_t sample_stride; /* DOC_TILED: 1 of every R tiles forms the threshold
                             sample (0 = auto, 1 = no sampling: every
                             document is a candidate) */
-  int32_t use_head;      /* DOC_TILED dense head on the tensor cores
-                            (requires 16 queries per group): 0 or 1 = on
-                            when the index has a head, -1 = off */
+  int32_t use_head;      /* DOC_TILED dense head (requires 16 queries per
+                            group and an index with a head): 0 = auto (FMAs
+                            for FP32 impacts, tensor-core MMAs otherwise),
+                            1 = CUDA-core FMAs, 2 = tensor-core MMAs,
+                            -1 = off */
   void* const* stage_events; /* NULL, or GS_NUM_STAGE_EVENTS cudaEvent_t */
 } gs_search_opts;
 

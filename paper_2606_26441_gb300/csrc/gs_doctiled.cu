@@ -43,10 +43,13 @@ constexpr int kMaxGroup = 64;                // queries per group (thresholds ke
 constexpr int kHeadG = 16;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 16;
 constexpr int kDefaultSampleStride = 32;
+// dense head kinds: none, CUDA-core FMAs, tensor-core MMAs
+enum { kHeadNone = 0, kHeadFma = 1, kHeadTensor = 2 };
 
 struct DtConfig {
   int G = 0, T = 0, m = 0, R = 0;  // R = 0: no sampling
   int H = 0;                        // dense head terms used (0: none)
+  int HK = kHeadNone;               // how the head is computed
   int ng = 0, nt = 0, n_sample = 0;
   int64_t sample_docs = 0;
   int64_t cap = 0;
@@ -60,10 +63,16 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0 || c->T > 8192) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
-  // the dense head (tensor cores) serves groups of kHeadG queries; use_head
-  // < 0 turns it off
+  // the dense head serves groups of kHeadG queries: FMAs (use_head 1, and
+  // FP32 impacts by default) or tensor-core MMAs (use_head 2, and the other
+  // impacts by default); use_head < 0 turns it off
   const int use_head = opts ? opts->use_head : 0;
+  if (use_head > 2) return GS_ERR_INVALID_ARG;
   const bool head = ix->head_H > 0 && G == kHeadG && use_head >= 0;
+  c->HK = !head ? kHeadNone
+                : (use_head == 1 ? kHeadFma
+                                 : (use_head == 2 ? kHeadTensor
+                                                  : (ix->impact == GS_IMPACT_F32 ? kHeadFma : kHeadTensor)));
   c->H = head ? ix->head_H : 0;
   G = head ? kHeadG : std::min(std::min(G, B), kMaxGroup);
   if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {
@@ -267,6 +276,9 @@ __device__ __forceinline__ float load_impact(const uint8_t* p) {
 
 // element j (0..3) of four consecutive stored impacts, as TF32 operand bits
 // (exact: FP16, BF16 and uint8 values have at most 11 significant bits)
+__device__ __forceinline__ float f4_get(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
 template <int IMPACT, typename V>
 __device__ __forceinline__ uint32_t impact_tf32(V v, int j) {
   if constexpr (IMPACT == GS_IMPACT_U8) {
@@ -287,7 +299,7 @@ __device__ __forceinline__ uint32_t impact_tf32(V v, int j) {
 // reduction address 32 distinct documents of one query row (consecutive
 // documents for dense terms: no bank conflicts), and every loaded posting
 // serves all of the group's queries holding the term.
-template <int IMPACT, int MODE, bool HEAD>
+template <int IMPACT, int MODE, int HK>
 __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const uint32_t* __restrict__ seg,
     int seg_tiles, int64_t N, const int32_t* __restrict__ q_indptr, int32_t B, int32_t q_nnz, int G, int T,
@@ -300,6 +312,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
+  constexpr bool HEAD = HK != kHeadNone;
   // dynamic shared memory: [G x T accumulators][staged query entries][item -> term]
   extern __shared__ __align__(16) uint8_t dyn_smem[];
   AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
@@ -315,10 +328,10 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
   __shared__ int s_next;
-  // head weights: FP32 impacts W[a][q] (a < nact rows, q < 16 queries);
-  // others as m16n8k8 A fragments [k-step][lane] (high part, low part)
+  // head weights: FMA head W[a][q] (a < nact rows, q < 16 queries);
+  // tensor-core head m16n8k8 A fragments [k-step][lane] (high part, low part)
   __shared__ uint4 s_af[HEAD ? (GS_MAX_HEAD_TERMS / 8) * 32 * 2 : 1];
-  float* s_w = reinterpret_cast<float*>(s_af);
+  AccT* s_w = reinterpret_cast<AccT*>(s_af);
   __shared__ int s_tc;  // the head runs on the tensor cores
   __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
@@ -361,18 +374,20 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     nact = head_nact[g];
     for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
     __syncthreads();
-    // FP32 impacts: W[a][q] for the FMA head.  Others: A fragments of
+    // FMA head: W[a][q].  Tensor-core head: A fragments of
     // W[q][a] (q < 16 queries, a < nact rows), k-step ks,
     // lane (gid, tig): W[gid][8 ks + tig], W[gid + 8][...], W[gid][8 ks + tig + 4],
     // W[gid + 8][...]; each weight w = high + low, both TF32.  uint8 weights
     // are integers: exact in TF32 and summed exactly in FP32 while every
     // partial sum stays below 2^24 (weights <= 1023, 255 per impact, <= 64 rows)
-    if (threadIdx.x == 0) s_tc = IMPACT != GS_IMPACT_F32;
+    if (threadIdx.x == 0) s_tc = HK == kHeadTensor;
     __syncthreads();
-    if (IMPACT == GS_IMPACT_F32)
-      for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x)
-        s_w[i] = __uint_as_float(__ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG)));
-    const int KS = IMPACT == GS_IMPACT_F32 ? 0 : (nact + 7) / 8;
+    if (HK == kHeadFma)
+      for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
+        const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
+        memcpy(&s_w[i], &raw, 4);
+      }
+    const int KS = HK == kHeadTensor ? (nact + 7) / 8 : 0;
     for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
       const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
       uint32_t hi[4], lo[4];
@@ -566,71 +581,99 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       // dense head: S[q][d] += sum_a W[q][a] X[a][d] over the group's active
       // head rows a, a contraction of 16 queries x nact rows x T documents.
       const int ib = impact_bytes(IMPACT);
-      if (IMPACT == GS_IMPACT_F32) {
-        // FP32 impacts: FMAs.  Thread (warp w, lane l) owns the 16 queries and
-        // documents 2 p, 2 p + 1 of each 1024-document slab, p = 32 w + l:
-        // the head rows are read coalesced, four rows in flight, the weights
-        // are warp-wide broadcasts, and every (query, document) cell has one
-        // owner (no atomics)
+      if (HK == kHeadFma) {
+        // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
+        // documents 2 p, 2 p + 1 of each slab of kSlab documents,
+        // p = 32 w + l: the head rows are read coalesced, four rows in
+        // flight, the weights are warp-wide broadcasts, and every (query,
+        // document) cell has one owner (no atomics)
         constexpr int kSlab = 2 * kDtThreads;
+        const int qh = 0;
         const int dp = warp * 32 + lane;
         for (int slab = 0; slab < T; slab += kSlab) {
-          if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
+          if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
           const int64_t col = doc0 + slab + 2 * dp;
-          float r[16][2];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0.f;
-          for (int a0 = 0; a0 < nact; a0 += 4) {
-            float2 xs[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              xs[u] = make_float2(0.f, 0.f);
-              if (a0 + u < nact)
-                xs[u] = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) +
-                                                              (int64_t)s_hact[a0 + u] * head_ld + col));
+          AccT r[16][2];
+  #pragma unroll
+          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
+          auto load2 = [&](int a, AccT& x0, AccT& x1) {
+            const int64_t at = (int64_t)s_hact[a] * head_ld + col;
+            if (IMPACT == GS_IMPACT_F32) {
+              const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
+              x0 = u.x;
+              x1 = u.y;
+            } else if (IMPACT == GS_IMPACT_U8) {
+              const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
+              x0 = (AccT)(u & 0xffu);
+              x1 = (AccT)(u >> 8);
+            } else {
+              const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
+              float2 f;
+              if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+              else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+              x0 = (AccT)f.x;
+              x1 = (AccT)f.y;
             }
-#pragma unroll
+          };
+          for (int a0 = 0; a0 < nact; a0 += 4) {
+            AccT xs[4][2];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              xs[u][0] = xs[u][1] = (AccT)0;
+              if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+            }
+  #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (a0 + u >= nact) break;
-              const float4* wr = reinterpret_cast<const float4*>(s_w + (a0 + u) * kHeadG);
-#pragma unroll
+              const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
+  #pragma unroll
               for (int q4 = 0; q4 < 4; ++q4) {
-                const float4 w4 = wr[q4];
-                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
+                AccT w4[4];
+                *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+  #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                  r[4 * q4 + v][0] = fmaf(wv[v], xs[u].x, r[4 * q4 + v][0]);
-                  r[4 * q4 + v][1] = fmaf(wv[v], xs[u].y, r[4 * q4 + v][1]);
+                  if (IMPACT == GS_IMPACT_U8) {
+                    r[4 * q4 + v][0] += w4[v] * xs[u][0];
+                    r[4 * q4 + v][1] += w4[v] * xs[u][1];
+                  } else {
+                    r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
+                    r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+                  }
                 }
               }
             }
           }
-#pragma unroll
+  #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            if (i < gq) {
-              float2* dst = reinterpret_cast<float2*>(acc + i * T + slab + 2 * dp);
-              float2 c = *dst;
-              c.x += r[i][0];
-              c.y += r[i][1];
-              *dst = c;
+            const int q = 16 * qh + i;
+            if (q < gq) {
+              AccT* dst = acc + q * T + slab + 2 * dp;
+              uint2 c = *reinterpret_cast<uint2*>(dst);
+              AccT* v = reinterpret_cast<AccT*>(&c);
+              v[0] += r[i][0];
+              v[1] += r[i][1];
+              *reinterpret_cast<uint2*>(dst) = c;
             }
           }
         }
       } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
-        // FP16, BF16 and uint8 impacts: m16n8k8 TF32 MMAs on the tensor
-        // cores, M = the 16 queries, K = 8 rows, N = 8 documents.  A warp
+        // tensor cores: m16n8k8 TF32 MMAs, M = the 16 queries, K = 8 rows,
+        // N = 8 documents.  A warp
         // step covers 32 documents base + 0..31 as four MMA tiles: column n
         // of tile j is document base + 4 n + j, so that lane (gid, tig)
         // reads documents base + 4 gid .. + 3 of a row with one vector load
         // (its B operand for all four tiles) and owns documents
         // base + 8 tig .. + 7 of queries gid, gid + 8 in the D fragments.
-        // Every (query, document) cell has one owner (no atomics).  The
-        // impacts are exact in TF32; W = high + low TF32 parts keeps FP32
-        // accuracy (uint8 weights are exact integers: high part only).
+        // Every (query, document) cell has one owner (no atomics).  W = high
+        // + low TF32 parts, and X too for FP32 impacts (FP16, BF16 and uint8
+        // impacts are exact in TF32), keeps FP32 accuracy; uint8 weights are
+        // exact integers and need the high part only.
         const int gid = lane >> 2, tig = lane & 3;
         const int KS = (nact + 7) / 8;
-        constexpr int KB = 4;  // k-steps whose operands are loaded together
-        using VecT = typename std::conditional<IMPACT == GS_IMPACT_U8, uint32_t, uint2>::type;
+        constexpr int KB = IMPACT == GS_IMPACT_F32 ? 2 : 4;  // k-steps whose operands are loaded together
+        using VecT = typename std::conditional<
+            IMPACT == GS_IMPACT_U8, uint32_t,
+            typename std::conditional<IMPACT == GS_IMPACT_F32, float4, uint2>::type>::type;
         for (int cb = warp * 32; cb < T; cb += kDtThreads) {
           const int64_t col = doc0 + cb + 4 * gid;
           float d[4][4];
@@ -659,9 +702,19 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               }
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                const uint32_t b0 = impact_tf32<IMPACT>(xv[u][0], j), b1 = impact_tf32<IMPACT>(xv[u][1], j);
-                if (IMPACT != GS_IMPACT_U8) mma_tf32(d[j], a_lo, b0, b1);
-                mma_tf32(d[j], a_hi, b0, b1);
+                if constexpr (IMPACT == GS_IMPACT_F32) {
+                  // x = high + low TF32 parts as well: three products
+                  const float x0 = f4_get(xv[u][0], j), x1 = f4_get(xv[u][1], j);
+                  const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
+                  const uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
+                  mma_tf32(d[j], a_lo, h0, h1);
+                  mma_tf32(d[j], a_hi, l0, l1);
+                  mma_tf32(d[j], a_hi, h0, h1);
+                } else {
+                  const uint32_t b0 = impact_tf32<IMPACT>(xv[u][0], j), b1 = impact_tf32<IMPACT>(xv[u][1], j);
+                  if (IMPACT != GS_IMPACT_U8) mma_tf32(d[j], a_lo, b0, b1);
+                  mma_tf32(d[j], a_hi, b0, b1);
+                }
               }
             }
           }
@@ -932,7 +985,7 @@ constexpr size_t kDynSmemFixed = kEntCap * sizeof(uint2) + (kItemCap + kChunkCap
 // Raises the dynamic shared-memory ceiling of both tile kernels of this
 // form, once per device: no attribute call is issued while a stream is
 // being captured for a graph.
-template <int IMPACT, bool HEAD>
+template <int IMPACT, int HK>
 gs_status tile_smem_attr() {
   static std::mutex mu;
   static bool done[128] = {};
@@ -942,32 +995,32 @@ gs_status tile_smem_attr() {
   if (dev < 0 || dev >= 128) return GS_ERR_UNSUPPORTED;
   if (!done[dev]) {
     const int ceil_bytes = (int)(kDtMaxAccBytes + kDynSmemFixed);
-    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeSample, HEAD>,
+    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeSample, HK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
-    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeMain, HEAD>,
+    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeMain, HK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
     done[dev] = true;
   }
   return GS_OK;
 }
 
-template <int IMPACT, bool HEAD>
+template <int IMPACT, int HK>
 gs_status tile_occupancy(const DtConfig& c, int* ctas) {
-  gs_status st = tile_smem_attr<IMPACT, HEAD>();
+  gs_status st = tile_smem_attr<IMPACT, HK>();
   if (st != GS_OK) return st;
   const size_t smem = (size_t)c.G * c.T * 4 + kDynSmemFixed;
-  GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, dt_tile_kernel<IMPACT, kModeMain, HEAD>,
+  GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, dt_tile_kernel<IMPACT, kModeMain, HK>,
                                                             kDtThreads, smem));
   return GS_OK;
 }
 
-template <int IMPACT, bool HEAD>
+template <int IMPACT, int HK>
 gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
                          const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
   const size_t smem = (size_t)c.G * c.T * 4 + kDynSmemFixed;
-  auto ks = dt_tile_kernel<IMPACT, kModeSample, HEAD>;
-  auto km = dt_tile_kernel<IMPACT, kModeMain, HEAD>;
-  gs_status st = tile_smem_attr<IMPACT, HEAD>();
+  auto ks = dt_tile_kernel<IMPACT, kModeSample, HK>;
+  auto km = dt_tile_kernel<IMPACT, kModeMain, HK>;
+  gs_status st = tile_smem_attr<IMPACT, HK>();
   if (st != GS_OK) return st;
   // tiles per CTA: enough CTAs for at least 16 waves of resident CTAs
   const int sms = ix->sms > 0 ? ix->sms : 1;
@@ -1007,8 +1060,9 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
 template <int IMPACT>
 gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
                        const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
-  if (c.H > 0) return launch_tiles_h<IMPACT, true>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
-  return launch_tiles_h<IMPACT, false>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
+  if (c.HK == kHeadFma) return launch_tiles_h<IMPACT, kHeadFma>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
+  if (c.HK == kHeadTensor) return launch_tiles_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
+  return launch_tiles_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
 }
 
 }  // namespace
@@ -1027,12 +1081,17 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
   out->cand_capacity = c.cap;
   out->head_terms = c.H;
   int ctas = 0;
-  const bool head = c.H > 0;
+  auto occ = [&](auto impact_tag) {
+    constexpr int I = decltype(impact_tag)::value;
+    if (c.HK == kHeadFma) return tile_occupancy<I, kHeadFma>(c, &ctas);
+    if (c.HK == kHeadTensor) return tile_occupancy<I, kHeadTensor>(c, &ctas);
+    return tile_occupancy<I, kHeadNone>(c, &ctas);
+  };
   switch (ix->impact) {
-    case GS_IMPACT_F32: st = head ? tile_occupancy<GS_IMPACT_F32, true>(c, &ctas) : tile_occupancy<GS_IMPACT_F32, false>(c, &ctas); break;
-    case GS_IMPACT_F16: st = head ? tile_occupancy<GS_IMPACT_F16, true>(c, &ctas) : tile_occupancy<GS_IMPACT_F16, false>(c, &ctas); break;
-    case GS_IMPACT_BF16: st = head ? tile_occupancy<GS_IMPACT_BF16, true>(c, &ctas) : tile_occupancy<GS_IMPACT_BF16, false>(c, &ctas); break;
-    default: st = head ? tile_occupancy<GS_IMPACT_U8, true>(c, &ctas) : tile_occupancy<GS_IMPACT_U8, false>(c, &ctas); break;
+    case GS_IMPACT_F32: st = occ(std::integral_constant<int, GS_IMPACT_F32>{}); break;
+    case GS_IMPACT_F16: st = occ(std::integral_constant<int, GS_IMPACT_F16>{}); break;
+    case GS_IMPACT_BF16: st = occ(std::integral_constant<int, GS_IMPACT_BF16>{}); break;
+    default: st = occ(std::integral_constant<int, GS_IMPACT_U8>{}); break;
   }
   if (st != GS_OK) return st;
   out->ctas_per_sm = ctas;

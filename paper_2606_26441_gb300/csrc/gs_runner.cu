@@ -77,8 +77,8 @@ std::vector<gs_search_opts> candidates(const gs_index* ix, const gs_search_opts&
     for (int G : {4, 8, 16}) {
       if ((int64_t)G * T > 16384) continue;
       if (G > bucket && G != 4) continue;
-      for (int head : {1, -1}) {
-        if (head == 1 && (G != 16 || ix->head_H == 0)) continue;
+      for (int head : {0, -1}) {
+        if (head == 0 && (G != 16 || ix->head_H == 0)) continue;
         for (int R : {16, 32, 64}) {
           gs_search_opts o = base;
           o.algo = GS_ALGO_DOC_TILED;

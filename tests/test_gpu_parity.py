@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 ALGOS = ["term_parallel", "doc_tiled"]
 # the doc-tiled kernel with and without the dense head
 VARIANTS = [("term_parallel", {}), ("doc_tiled", {}), ("doc_tiled", {"use_head": -1}),
-            ("doc_tiled", {"use_head": 1}), ("doc_parallel", {})]
+            ("doc_tiled", {"use_head": 1}), ("doc_tiled", {"use_head": 2}), ("doc_parallel", {})]
 
 
 def _gs():
@@ -144,9 +144,9 @@ def test_doc_tiled_keeps_two_ctas_per_sm(impact):
     idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
                             torch.from_numpy(docs.weights).to(dev), docs.vocab, impact)
     try:
-        for use_head in (1, -1):
+        for use_head in (0, 1, 2, -1):
             for G, T in ((16, 1024), (8, 2048), (4, 4096)):
-                if use_head > 0 and G != 16:
+                if use_head >= 0 and G != 16:
                     continue
                 plan = idx.plan(64, 64 * 30, 100, gs.make_opts("doc_tiled", group_queries=G, tile_docs=T,
                                                                use_head=use_head))
@@ -247,6 +247,22 @@ def test_edge_cases():
     c = Case(docs, single, "f32", tile_docs=256)
     for algo in ALGOS:
         c.check(5, algo)
+
+
+def test_u8_head_with_large_summed_weights():
+    """A query repeating a head term sums its quantized weights past the
+    range in which the tensor-core head sums exactly in FP32; that group
+    takes the integer FMA head, and the result stays bit-exact."""
+    docs = synth.docs(20_000, seed=5)
+    top = int(np.argmax(np.bincount(docs.terms, minlength=docs.vocab)))
+    base = synth.queries(20, seed=5)
+    rows = [([top] * 12, [5.0] * 12)] + [tuple(map(list, base.row(i))) for i in range(1, 20)]
+    indptr = np.cumsum([0] + [len(r[0]) for r in rows]).astype(np.int64)
+    qs = synth.SparseBatch(indptr, np.array(sum([list(r[0]) for r in rows], []), np.int32),
+                           np.array(sum([list(r[1]) for r in rows], []), np.float32))
+    c = Case(docs, qs, "u8")
+    for kw in ({}, {"use_head": 2}, {"use_head": 1}):
+        c.check(100, "doc_tiled", **kw)
 
 
 def test_bad_query_terms_are_flagged():
