@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--workload", default="docs8.8m_b500_top1000", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--headline", default="f32:doc_tiled", help="impact:algo of the reported value")
     ap.add_argument("--forms", default="f32:term_parallel,u8:doc_tiled,f16:doc_tiled,bf16:doc_tiled",
-                    help="other impact:algo forms measured beside the headline ('' = none)")
+                    help="other impact:algo[:opt=v;opt=v] forms measured beside the headline ('' = none); "
+                         "opts are gs_search_opts fields, e.g. f32:doc_tiled:use_head=2")
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -226,14 +227,15 @@ def sample_term_counts(docs, T, R, n_sample):
     return cnt
 
 
-def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sample_clocks=False):
+def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sample_clocks=False, opts_kw=None):
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_NUM_STAGE_EVENTS)] for _ in range(steps)]
     for e in ev:  # torch creates the CUDA event on its first record; the library re-records it
         for x in e:
             x.record()
     torch.cuda.synchronize()
-    opts_plain = gs.make_opts(algo)
-    opts_t = [gs.make_opts(algo, stage_events=e) for e in ev]
+    kw = opts_kw or {}
+    opts_plain = gs.make_opts(algo, **kw)
+    opts_t = [gs.make_opts(algo, stage_events=e, **kw) for e in ev]
     ws = gs.alloc_workspace(idx, q.batch, q.nnz, k, opts_plain)
     out_ids = torch.empty((q.batch, k), dtype=torch.int32, device=q.indptr.device)
     out_sc = torch.empty((q.batch, k), dtype=idx.score_dtype, device=q.indptr.device)
@@ -313,20 +315,22 @@ def run_gpu(args, w, docs, qs, world, rank, local):
     df = np.bincount(docs.terms, minlength=docs.vocab).astype(np.int64)
 
     head_imp, head_algo = args.headline.split(":")
-    forms = [(head_imp, head_algo)] + [tuple(f.split(":")) for f in args.forms.split(",") if f]
+    forms = [args.headline] + [f for f in args.forms.split(",") if f]
     indexes = {}
     results = {}
-    for imp, algo in forms:
+    for form in forms:
+        imp, algo, *rest = form.split(":")
+        kw = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in rest[0].split(";")} if rest else {}
         if imp not in indexes:
             indexes[imp] = gs.gs_index_build(d_indptr, d_terms, d_w, docs.vocab, imp)
         idx = indexes[imp]
         r = time_form(gs, torch, idx, q, k, algo, args.steps, args.warmup, dist, local,
-                      sample_clocks=(imp, algo) == (head_imp, head_algo))
-        plan = idx.plan(q.batch, q.nnz, k, gs.make_opts(algo))
-        results[(imp, algo)] = (r, plan, idx)
+                      sample_clocks=form == args.headline, opts_kw=kw)
+        plan = idx.plan(q.batch, q.nnz, k, gs.make_opts(algo, **kw))
+        results[form] = (r, plan, idx)
 
     # headline
-    r, plan, idx = results[(head_imp, head_algo)]
+    r, plan, idx = results[args.headline]
     span_s = reduce_max_over_ranks(r["span_ms"] / 1e3, dist, dev)
     value = w.batch * args.steps * world / span_s
     st = idx.stats()
@@ -343,9 +347,10 @@ def run_gpu(args, w, docs, qs, world, rank, local):
     upd_df = df - layout_info["sample_df"] if head_algo == "doc_tiled" else df
     updates = int(upd_df[qs.terms].sum())
     forms_out = {}
-    for (imp, algo), (rr, pl, ix) in results.items():
+    for form, (rr, pl, ix) in results.items():
+        algo = form.split(":")[1]
         ms = rr["per_step_ms"]
-        forms_out[f"{imp}:{algo}"] = {
+        forms_out[form] = {
             "qps": w.batch * len(ms) / (rr["span_ms"] / 1e3), "p50_ms": float(np.percentile(ms, 50)),
             "p99_ms": float(np.percentile(ms, 99)), "per_query_ms": float(np.mean(ms)) / w.batch,
             "stage_ms": dict(zip(stage_names if algo == "doc_tiled" else

@@ -658,29 +658,29 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         }
       } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
         // tensor cores: m16n8k8 TF32 MMAs, M = the 16 queries, K = 8 rows,
-        // N = 8 documents.  A warp
-        // step covers 32 documents base + 0..31 as four MMA tiles: column n
-        // of tile j is document base + 4 n + j, so that lane (gid, tig)
-        // reads documents base + 4 gid .. + 3 of a row with one vector load
-        // (its B operand for all four tiles) and owns documents
-        // base + 8 tig .. + 7 of queries gid, gid + 8 in the D fragments.
-        // Every (query, document) cell has one owner (no atomics).  W = high
-        // + low TF32 parts, and X too for FP32 impacts (FP16, BF16 and uint8
-        // impacts are exact in TF32), keeps FP32 accuracy; uint8 weights are
-        // exact integers and need the high part only.
-        const int gid = lane >> 2, tig = lane & 3;
-        const int KS = (nact + 7) / 8;
+        // N = 8 documents.  A warp step covers 8 NT documents base + 0.. as
+        // NT MMA tiles: column n of tile j is document base + NT n + j, so
+        // that lane (gid, tig) reads documents base + NT gid .. + NT - 1 of a
+        // row with one vector load (its B operand for all NT tiles) and owns
+        // documents base + 2 NT tig .. + 2 NT - 1 of queries gid, gid + 8 in
+        // the D fragments.  Every (query, document) cell has one owner (no
+        // atomics).  W = high + low TF32 parts, and X too for FP32 impacts
+        // (FP16, BF16 and uint8 impacts are exact in TF32), keeps FP32
+        // accuracy; uint8 weights are exact integers: high part only.
+        constexpr int NT = 4;
         constexpr int KB = IMPACT == GS_IMPACT_F32 ? 2 : 4;  // k-steps whose operands are loaded together
         using VecT = typename std::conditional<
             IMPACT == GS_IMPACT_U8, uint32_t,
             typename std::conditional<IMPACT == GS_IMPACT_F32, float4, uint2>::type>::type;
-        for (int cb = warp * 32; cb < T; cb += kDtThreads) {
-          const int64_t col = doc0 + cb + 4 * gid;
-          float d[4][4];
+        const int gid = lane >> 2, tig = lane & 3;
+        const int KS = (nact + 7) / 8;
+        for (int cb = warp * 8 * NT; cb < T; cb += kDtThreads / 32 * 8 * NT) {
+          const int64_t col = doc0 + cb + NT * gid;
+          float d[NT][4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
+          for (int j = 0; j < NT; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
           for (int k0 = 0; k0 < KS; k0 += KB) {
-            VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, four documents each
+            VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, NT documents each
 #pragma unroll
             for (int u = 0; u < KB; ++u)
 #pragma unroll
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                 a_lo[0] = al.x; a_lo[1] = al.y; a_lo[2] = al.z; a_lo[3] = al.w;
               }
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = 0; j < NT; ++j) {
                 if constexpr (IMPACT == GS_IMPACT_F32) {
                   // x = high + low TF32 parts as well: three products
                   const float x0 = f4_get(xv[u][0], j), x1 = f4_get(xv[u][1], j);
@@ -718,15 +718,15 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               }
             }
           }
-          // D: (query gid + 8 h, documents cb + 8 tig + 4 c + j) = d[j][2 h + c]
+          // D: (query gid + 8 h, document cb + 2 NT tig + NT c + j) = d[j][2 h + c]
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int q = gid + 8 * h;
             if (q >= gq) continue;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              AccT* dst = acc + q * T + cb + 8 * tig + 4 * c;
-              if (IMPACT == GS_IMPACT_U8) {
+              AccT* dst = acc + q * T + cb + 2 * NT * tig + NT * c;
+              if constexpr (IMPACT == GS_IMPACT_U8) {
                 int4 v = *reinterpret_cast<int4*>(dst);
                 v.x += __float2int_rn(d[0][2 * h + c]);
                 v.y += __float2int_rn(d[1][2 * h + c]);
