@@ -18,6 +18,7 @@ benchmark) on the host cores on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -61,6 +62,40 @@ def cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_dt_tile_kernel_docs8.8m_b500_top1000.md")
+KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh")
+
+
+def kernel_source_digest():
+    """sha256 over the doc-tiled kernel's source files (in KERNEL_SOURCES order)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_26441_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload, form):
+    """DRAM bytes (read + write) per main-pass launch from the committed ncu capture,
+    or None when that capture is of another workload or form, or the kernel source has
+    changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    rec = {}
+    for line in open(TRAFFIC_FILE):
+        if line.startswith("- ") and ": " in line:
+            key, val = line[2:].split(": ", 1)
+            rec[key.strip()] = val.strip().strip("`")
+    try:
+        if rec.get("workload") != workload or rec.get("form") != form:
+            return None
+        if rec.get("kernel source sha256") != kernel_source_digest():
+            return None
+        return int(rec["dram bytes per main-pass launch"])
+    except (KeyError, ValueError, OSError):
+        return None
 
 
 def load_peaks():
@@ -370,7 +405,8 @@ def run_gpu(args, w, docs, qs, world, rank, local):
         "roofline": {"bound": "hbm", "kernel": "dt_tile_kernel (main pass)" if head_algo == "doc_tiled"
                      else "tp_scatter_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                     "traffic": None, "algorithmic_bytes": alg_bytes, "kernel_ms": kern_ms,
+                     "traffic": recorded_traffic(w.name, args.headline), "algorithmic_bytes": alg_bytes,
+                     "kernel_ms": kern_ms,
                      "postings_read": extra["postings"], "scatter_updates": updates,
                      "updates_per_s": updates / (kern_ms / 1e3)},
         "gpu_launches": int(r["launches"]),
