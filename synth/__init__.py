@@ -186,7 +186,7 @@ WORKLOADS = {
                                 {"batches": (1, 8, 64, 256, 1024), "ks": (10, 100, 1000)}),
     # serving: 1M and 8.84M documents resident (FP16), Poisson arrivals at several rates
     "serving_1m_8.8m": Workload("serving_1m_8.8m", N_8_8M, 256, 1000, ("f16",), MIXTURE_LAW,
-                                {"rates": (200, 1000, 2000, 5000), "seconds": 3.0}),
+                                {"rates": (200, 1000, 2000, 5000, 10000, 20000), "seconds": 3.0}),
     # document sparsity sweep: 500K docs with exactly n terms each, 64 queries, top-1000
     "sparsity_500k_b64": Workload("sparsity_500k_b64", 500_000, 64, 1000, ("f32",), QUERY_LAW,
                                   {"doc_nnz": (10, 50, 100, 200, 500)}),

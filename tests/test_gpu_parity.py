@@ -342,6 +342,40 @@ def test_medium_workload_1m():
         c.idx.free()
 
 
+def test_reduced_precision_error_vs_fp64():
+    """Each impact form's error against the FP64 oracle on the FP32 impacts (the
+    unrounded scores), 1M documents, 32 queries, top-1000 on the doc-tiled path.
+
+    Gate: every form matches the FP64 oracle on its own stored impacts (uint8
+    bit-exact, floats within tau).  Report (printed): the largest and mean error of
+    the returned scores against the unrounded FP64 scores, relative to
+    A = sum |w x|, and recall of the unrounded exact top-1000."""
+    docs = synth.docs(1_000_000, seed=0)
+    qs = synth.queries(32, seed=0)
+    k = 1000
+    truth = oracle.OracleIndex.from_batch(docs, "f32")
+    tid, _, _ = truth.topk(qs.indptr, qs.terms, qs.weights, k)
+    report = []
+    for impact in ("f32", "f16", "bf16", "u8"):
+        c = Case(docs, qs, impact)
+        c.check(k, "doc_tiled")
+        ids, sc, flags = c.search(k, "doc_tiled")
+        assert flags == 0
+        s_true, a_true = truth.doc_scores(qs.indptr, qs.terms, qs.weights, ids.astype(np.int32))
+        scale = 1.0 / (51.0 * 51.0) if impact == "u8" else 1.0  # uint8: round(51 w) x round(51 x)
+        rel = np.abs(sc.astype(np.float64) * scale - s_true) / np.maximum(a_true, 1e-30)
+        recall = np.mean([len(set(ids[q].tolist()) & set(tid[q].tolist())) / k for q in range(qs.n)])
+        report.append((impact, float(rel.max()), float(rel.mean()), float(recall)))
+        c.idx.free()
+    print("\nimpact | max |s - s64|/A | mean |s - s64|/A | recall@1000 of the unrounded top-1000")
+    for impact, mx, mean, rec in report:
+        print(f"{impact} | {mx:.3e} | {mean:.3e} | {rec:.4f}")
+    by = {r[0]: r for r in report}
+    assert by["f32"][1] <= 1e-5 + 1e-6 and by["f32"][3] >= 0.999
+    for impact in ("f16", "bf16", "u8"):
+        assert by[impact][3] >= 0.8, by[impact]
+
+
 def test_runner_graph_replay_matches_search():
     """Uneven batches through captured graphs (autotuned plans) equal the direct search."""
     gs = _gs()
