@@ -112,9 +112,10 @@ typedef struct {
                          0 = default (1024); -1 = build no table */
   int32_t head_terms; /* dense head: the H terms with the longest posting
                          lists also get a dense [H x N] impact matrix that the
-                         doc-tiled kernel multiplies with FMAs instead of
-                         scattering them; 0 = default (32), -1 = none,
-                         at most GS_MAX_HEAD_TERMS */
+                         doc-tiled kernel multiplies (FMAs or tensor-core
+                         MMAs) instead of scattering them; 0 = default (32
+                         for FP32 impacts, 64 otherwise), -1 = none, at most
+                         GS_MAX_HEAD_TERMS */
   int32_t doc_major;  /* 1: also keep a document-major copy (doc CSR of stored
                          impacts) for the DOC_PARALLEL kernel */
   int32_t reserved[5];
