@@ -42,7 +42,7 @@ constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting 
 constexpr int kMaxGroup = 64;                // queries per group (thresholds kept in shared memory)
 constexpr int kHeadG = 16;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 16;
-constexpr int kDefaultSampleStride = 32;
+constexpr int kDefaultSampleStride = 64;
 // dense head kinds: none, CUDA-core FMAs, tensor-core MMAs
 enum { kHeadNone = 0, kHeadFma = 1, kHeadTensor = 2 };
 

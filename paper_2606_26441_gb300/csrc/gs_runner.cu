@@ -79,7 +79,7 @@ std::vector<gs_search_opts> candidates(const gs_index* ix, const gs_search_opts&
       if (G > bucket && G != 4) continue;
       for (int head : {0, -1}) {
         if (head == 0 && (G != 16 || ix->head_H == 0)) continue;
-        for (int R : {16, 32, 64}) {
+        for (int R : {32, 64, 128}) {
           gs_search_opts o = base;
           o.algo = GS_ALGO_DOC_TILED;
           o.tile_docs = T;
