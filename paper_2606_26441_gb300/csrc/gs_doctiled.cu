@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int32_t s_len[kDtThreads];         // postings in the segment
   __shared__ int32_t s_item[kDtThreads + 1];
   __shared__ int32_t s_tp[kDtThreads + 1];     // packed position of each short segment
-  __shared__ int32_t s_e0[kDtThreads], s_e1[kDtThreads];
+  __shared__ int32_t s_e0[kDtThreads + 1];  // entries of term j: [s_e0[j], s_e0[j + 1])
   __shared__ uint32_t s_theta[kMaxGroup];
   __shared__ int warp_buf[32];
   __shared__ int s_next;
@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int s_tc;  // the head runs on the tensor cores
   __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
-  __shared__ int32_t s_t[kDtThreads];  // the group's first terms
+  __shared__ int32_t s_t[kDtThreads];   // the group's terms (one batch)
+  __shared__ int32_t s_tb[kDtThreads];  // and their first index blocks
 
   // the CTA scores tiles [tile_begin, tile_end) of query group g; the
   // group's data are read once and serve all of them
@@ -366,8 +367,15 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   // terms per batch: their 128-posting work items must fit the item table
   const int items_per_term = T / 128 + 1;
   const int tb = min(kDtThreads, kItemCap / items_per_term);
-  if ((int)threadIdx.x < tb && (int)threadIdx.x < nterm) {
-    s_t[threadIdx.x] = ut[threadIdx.x];
+  // a group whose terms fit one batch keeps their ids, first blocks and entry
+  // ranges for all its tiles; only the segment bounds are read per tile
+  const bool one_batch = nterm <= tb;
+  if (one_batch && (int)threadIdx.x < nterm) {
+    const int32_t t = ut[threadIdx.x];
+    s_t[threadIdx.x] = t;
+    s_tb[threadIdx.x] = (int32_t)__ldg(term_block + t);
+    s_e0[threadIdx.x] = __ldg(up + threadIdx.x);
+    if ((int)threadIdx.x == nterm - 1) s_e0[nterm] = __ldg(up + nterm);
   }
   int nact = 0;
   if (HEAD) {
@@ -444,20 +452,25 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       const int j = j0 + threadIdx.x;
       int items = 0, tiny = 0;
       if (threadIdx.x < tb && j < nterm) {
-        const int32_t t = j0 == 0 ? s_t[threadIdx.x] : ut[j];
+        const int32_t t = one_batch ? s_t[threadIdx.x] : ut[j];
         const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
         const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
-        s_p0[threadIdx.x] = blocks + (__ldg(term_block + t) + (int64_t)(s >> 5)) * bb;
+        const int64_t tblk = one_batch ? (int64_t)s_tb[threadIdx.x] : __ldg(term_block + t);
+        s_p0[threadIdx.x] = blocks + (tblk + (int64_t)(s >> 5)) * bb;
         s_off[threadIdx.x] = (int32_t)(s & 31u);
         s_len[threadIdx.x] = (int32_t)(e - s);
-        s_e0[threadIdx.x] = __ldg(up + j);
-        s_e1[threadIdx.x] = __ldg(up + j + 1);
+        if (!one_batch) {
+          s_e0[threadIdx.x] = __ldg(up + j);
+          if ((int)threadIdx.x == tb - 1 || j == nterm - 1) s_e0[threadIdx.x + 1] = __ldg(up + j + 1);
+        }
         if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
         else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
       }
-      int total, tiny_total;
-      const int xi = block_excl_scan(items, warp_buf, &total);
-      const int xt = block_excl_scan(tiny, warp_buf, &tiny_total);
+      // one scan of both counts: items (< 2^16 per batch) low, short postings high
+      int tot2;
+      const int x2 = block_excl_scan(items | (tiny << 16), warp_buf, &tot2);
+      const int xi = x2 & 0xffff, xt = x2 >> 16;
+      const int total = tot2 & 0xffff, tiny_total = tot2 >> 16;
       if (threadIdx.x < tb) {
         s_item[threadIdx.x] = xi;
         s_tp[threadIdx.x] = xt;
@@ -511,7 +524,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       };
       // NI loaded items of term jj: every entry of the term, every posting
       auto score_items = [&](int jj, const int* da, const AccT* x, int ni) {
-        const int32_t eb = s_e0[jj], ee = s_e1[jj];
+        const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
         for (int32_t en = eb; en < ee; ++en) {
           const uint2 E = entry(en);
           const uint32_t row = acc_s + E.x;
@@ -535,7 +548,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         AccT xv;
         if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
         else xv = (AccT)load_x<IMPACT>(blk, li);
-        const int32_t eb = s_e0[jj], ee = s_e1[jj];
+        const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
         for (int32_t en = eb; en < ee; ++en) {
           const uint2 E = entry(en);
           red(acc_s + E.x + da, E.y, xv);

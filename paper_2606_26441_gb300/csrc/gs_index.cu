@@ -388,6 +388,9 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
     return cuda_fail(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
   ix->total_blocks = ix->h_term_block[vocab];
+  // block indices are kept as int32 by the scoring kernels (2^31 blocks would be
+  // 68.7 G postings, more than the device holds)
+  if (ix->total_blocks > (int64_t)INT32_MAX) return fail(GS_ERR_UNSUPPORTED);
 
   // 5. blocks: padding everywhere, then postings in doc order
   const int64_t nb_alloc = std::max<int64_t>(ix->total_blocks, 1);
