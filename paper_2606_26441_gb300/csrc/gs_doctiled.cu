@@ -37,7 +37,7 @@ constexpr int kDtThreads = 512;                  // two CTAs per SM (64 register
 constexpr int kDtMaxAccBytes = 64 * 1024;     // G x T accumulators
 constexpr int kEntCap = 1280;                // query entries staged in shared memory (10 KB)
 constexpr int kItemCap = 4608;               // (term, 128-posting chunk) items per term batch (9 KB)
-constexpr int kTinySeg = 64;                 // segments shorter than this are packed, not itemised
+constexpr int kTinySeg = 32;                 // segments shorter than this are packed, not itemised
 constexpr int kChunkCap = kDtThreads * kTinySeg / 32 + 1;  // packed 32-posting chunks per term batch
 constexpr int kMaxGroup = 64;                // queries per group (thresholds kept in shared memory)
 constexpr int kHeadG = 16;                   // queries per group when the dense head is used
