@@ -13,9 +13,9 @@
 // segment.
 //
 // Exact top-k without dense rows: every R-th full tile is a sample tile.  The
-// sample tiles are scored first and written out; the k-th largest sample
-// score theta_q of each query is a lower bound of its k-th largest score over
-// all documents.  The remaining tiles are then scored, and every document
+// sample tiles are scored first and written out; theta_q, the k-th largest
+// sample score of query q rounded down to 22 key bits, is a lower bound of
+// its k-th largest score over all documents.  The remaining tiles are then scored, and every document
 // with score > theta_q is appended to a per-query candidate list; documents
 // equal to theta_q set a bit in a per-query tie bitmap.  A final kernel per
 // query returns the top-k of the candidates by (score desc, id asc), taking
@@ -105,7 +105,7 @@ struct DtPlan {
   int32_t* n_u;       // [ng]
   uint2* ent;         // [q_nnz] (query within group, weight bits)
   uint32_t* samp;     // [B][sample_docs]
-  uint32_t* theta;    // [B] k-th largest sample score (raw bits)
+  uint32_t* theta;    // [B] lower bound of the k-th largest sample score (raw bits)
   uint2* cand;        // [B][cap] (key, doc)
   uint32_t* cand_cnt; // [B]
   uint32_t* tiebm;    // [B][bm_words]

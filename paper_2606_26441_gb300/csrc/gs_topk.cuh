@@ -4,6 +4,8 @@
 // and a bitonic sort of the k winners by (key desc, id asc).
 #pragma once
 
+#include <type_traits>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -162,14 +164,14 @@ __device__ __forceinline__ void select_topk_candidates(Get get, int64_t n, int k
 template <typename ST>
 __device__ __forceinline__ uint32_t radix_kth_key(const ST* __restrict__ r, int64_t N, int k,
                                                   uint32_t (*hist)[2048], int* warp_buf, uint32_t* s_digit_p,
-                                                  int* s_need_p, int* need_out) {
+                                                  int* s_need_p, int* need_out, int passes = 3) {
   uint32_t& s_digit = *s_digit_p;
   int& s_need = *s_need_p;
   const int lane = threadIdx.x & 31;
   const int copy = (threadIdx.x >> 5) % kHistCopies;
   uint32_t prefix = 0, pmask = 0;
   int need = k;
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
     const int nb = pass == 2 ? 1024 : 2048;
     for (int i = threadIdx.x; i < kHistCopies * 2048; i += blockDim.x) (&hist[0][0])[i] = 0;
@@ -293,8 +295,12 @@ __global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST*
   }
 }
 
-// The k-th largest score of each of `rows` dense rows (raw score bits), no
-// collection or sort: the threshold the doc-tiled path needs from its sample.
+// A lower bound of the k-th largest score of each of `rows` dense rows (raw
+// score bits).  Float scores: the k-th largest key with its 10 low bits
+// cleared, the lower edge of its bin after two radix passes (22 key bits);
+// the bin is 2^-13 of the score wide, so it admits few extra candidates.
+// Integer scores: the k-th largest score itself (three passes).  The
+// doc-tiled path needs only a lower bound from its sample.
 template <typename ST>
 __global__ void __launch_bounds__(kTopkThreads) kth_score_rows_kernel(const ST* __restrict__ S, int64_t ld, int64_t N,
                                                                       int k, uint32_t* __restrict__ out_bits) {
@@ -303,7 +309,9 @@ __global__ void __launch_bounds__(kTopkThreads) kth_score_rows_kernel(const ST* 
   __shared__ uint32_t s_digit;
   __shared__ int s_need;
   int need = k;
-  const uint32_t key = radix_kth_key(S + (int64_t)blockIdx.x * ld, N, k, hist, warp_buf, &s_digit, &s_need, &need);
+  const int passes = std::is_same<ST, float>::value ? 2 : 3;
+  const uint32_t key =
+      radix_kth_key(S + (int64_t)blockIdx.x * ld, N, k, hist, warp_buf, &s_digit, &s_need, &need, passes);
   if (threadIdx.x == 0) {
     const ST v = key_to_score<ST>(key);
     uint32_t bits;
