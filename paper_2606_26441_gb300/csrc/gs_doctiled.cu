@@ -112,6 +112,8 @@ struct DtPlan {
   uint32_t* headw;    // [ng][H][kHeadG] head weights (float or int bits)
   int32_t* head_act;  // [ng][H] head rows with a non-zero weight
   int32_t* head_nact; // [ng]
+  int32_t* fixp;      // [ng] 1: fixed-point tail
+  int32_t* qscale;    // [B] S_q of the fixed-point tail
 };
 
 DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const DtConfig& c, size_t* bytes) {
@@ -130,6 +132,8 @@ DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const
   p.headw = cv.take<uint32_t>((size_t)c.ng * std::max(c.H, 1) * kHeadG);
   p.head_act = cv.take<int32_t>((size_t)c.ng * std::max(c.H, 1));
   p.head_nact = cv.take<int32_t>(c.ng);
+  p.fixp = cv.take<int32_t>(c.ng);
+  p.qscale = cv.take<int32_t>(B);
   *bytes = cv.size();
   return p;
 }
@@ -154,8 +158,13 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
                                                        int32_t* __restrict__ n_u, uint2* __restrict__ ent,
                                                        const int32_t* __restrict__ head_slot, int H,
                                                        uint32_t* __restrict__ headw, int32_t* __restrict__ head_act,
-                                                       int32_t* __restrict__ head_nact, uint32_t* flags) {
+                                                       int32_t* __restrict__ head_nact,
+                                                       const float* __restrict__ max_abs, int32_t* __restrict__ fixp,
+                                                       int32_t* __restrict__ qscale, uint32_t* flags) {
   __shared__ int warp_buf[32];
+  __shared__ float s_U[kMaxGroup];  // per query: sum over tail entries of |w| max|x|
+  __shared__ int s_n[kMaxGroup];    // per query: tail entries
+  __shared__ int s_ok;
   const int g = blockIdx.x;
   const int q0 = g * G, q1 = min(B, q0 + G);
   uint32_t fl = 0;
@@ -170,6 +179,11 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
   for (int t = threadIdx.x; t < V; t += blockDim.x) cnt[t] = 0u;
   uint32_t* hw = headw + (int64_t)g * H * kHeadG;
   for (int i = threadIdx.x; i < H * kHeadG; i += blockDim.x) hw[i] = 0u;
+  for (int i = threadIdx.x; i < kMaxGroup; i += blockDim.x) {
+    s_U[i] = 0.f;
+    s_n[i] = 0;
+  }
+  if (threadIdx.x == 0) s_ok = impact != GS_IMPACT_U8;
   __syncthreads();
   for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int32_t t = q_terms[e];
@@ -217,7 +231,33 @@ __global__ void __launch_bounds__(1024) dt_prep_kernel(const int32_t* __restrict
     const uint32_t pos = atomicAdd(&cnt[t], 1u);
     const uint32_t wb = impact == GS_IMPACT_U8 ? (uint32_t)quant_u8(w) : __float_as_uint(w);
     ent[pos] = make_uint2((uint32_t)ql, wb);
+    if (impact != GS_IMPACT_U8) {
+      atomicAdd(&s_U[ql], fabsf(w) * __ldg(max_abs + t));
+      atomicAdd(&s_n[ql], 1);
+    }
   }
+  // Fixed-point tail (float impacts): query q's tail products w x are added as
+  // integers round(w x 2^S_q).  With U_q >= sum |w| max|x| over its n_q tail
+  // entries, 2^S_q <= (2^31 - 2^10 - n_q) / U_q keeps every partial sum inside
+  // int32, and the rounding error n_q 2^-(S_q + 1) must stay within 0.9e-6 (the
+  // tolerance's absolute term); otherwise the group keeps float reductions.
+  __syncthreads();
+  const int gq = q1 - q0;
+  if ((int)threadIdx.x < gq && impact != GS_IMPACT_U8) {
+    const float U = s_U[threadIdx.x] * (1.0f + 1.0f / 1024.0f);  // margin for the float sum of U
+    const int n = s_n[threadIdx.x];
+    int S = 60;
+    if (n > 0) {
+      S = (int)floorf(log2f((2147483648.0f - 1024.0f - (float)n) / U));
+      S = max(min(S, 60), -60);
+      // the bound used 2^S <= (2^31 - 2^10 - n) / U: step down if log2f rounded up
+      while (S > -60 && ldexpf(U, S) > 2147483648.0f - 1024.0f - (float)n) --S;
+      if ((float)n * ldexpf(1.0f, -(S + 1)) > 0.9e-6f) s_ok = 0;
+    }
+    qscale[q0 + threadIdx.x] = S;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) fixp[g] = s_ok;
   // head rows some query of the group uses
   if (H > 0) {
     __syncthreads();
@@ -291,6 +331,11 @@ __device__ __forceinline__ uint32_t impact_tf32(V v, int j) {
   }
 }
 
+// a score cell of the tail: the float itself, or a fixed-point integer times 2^-S
+__device__ __forceinline__ float tail_value(float v, bool fx, float isc) {
+  return fx ? (float)__float_as_int(v) * isc : v;
+}
+
 // One CTA per (tile, group): G x T score block in shared memory.
 //
 // Work items are (term, chunk of 4 posting blocks = 128 postings) pairs of
@@ -309,7 +354,8 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     int64_t sample_docs, const uint32_t* __restrict__ theta, int k, uint2* __restrict__ cand,
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
     const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
-    const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles) {
+    const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles,
+    const int32_t* __restrict__ fixp, const int32_t* __restrict__ qscale) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
   constexpr bool HEAD = HK != kHeadNone;
@@ -326,6 +372,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int32_t s_tp[kDtThreads + 1];     // packed position of each short segment
   __shared__ int32_t s_e0[kDtThreads + 1];  // entries of term j: [s_e0[j], s_e0[j + 1])
   __shared__ uint32_t s_theta[kMaxGroup];
+  __shared__ float s_sc[kMaxGroup], s_isc[kMaxGroup];  // fixed-point tail: 2^S_q and 2^-S_q
   __shared__ int warp_buf[32];
   __shared__ int s_next;
   // head weights: FMA head W[a][q] (a < nact rows, q < 16 queries);
@@ -353,6 +400,17 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   const int nterm = n_u[g];
   const int32_t* ut = u_terms + ebase;
   const int32_t* up = u_ptr + ebase + g;
+  // fixed-point tail (float impacts, groups whose bound allows it): staged
+  // weights carry the query's scale 2^S_q, rows hold integers until the head
+  // phase (or a conversion pass) turns them into floats
+  const bool fx = IMPACT != GS_IMPACT_U8 && __ldg(fixp + g) != 0;
+  if (fx)
+    for (int i = threadIdx.x; i < gq; i += blockDim.x) {
+      const int S = __ldg(qscale + q0 + i);
+      s_sc[i] = ldexpf(1.0f, S);
+      s_isc[i] = ldexpf(1.0f, -S);
+    }
+  __syncthreads();
   // the group's (query, weight) entries, staged with the query's row byte offset
   const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
   const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
@@ -361,7 +419,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   if (staged)
     for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) {
       const uint2 E = __ldg(ent + ent_lo + i);
-      ent_s[i] = make_uint2(E.x * row_bytes, E.y);
+      ent_s[i] = make_uint2(E.x * row_bytes, fx ? __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]) : E.y);
     }
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
   // terms per batch: their 128-posting work items must fit the item table
@@ -490,15 +548,23 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           E = ent_s[en - ent_lo];
         } else {
           E = __ldg(ent + en);
+          if (fx) E.y = __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]);
           E.x *= row_bytes;
         }
         return E;
       };
-      auto red = [&](uint32_t addr, uint32_t wbits, AccT xv) {
-        if (IMPACT == GS_IMPACT_U8)
+      // one update w x: integer reductions (uint8 impacts, and float impacts
+      // in fixed point, w already scaled by 2^S_q), else float reductions
+      auto red = [&](auto fxc, uint32_t addr, uint32_t wbits, AccT xv) {
+        if constexpr (IMPACT == GS_IMPACT_U8) {
           asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
-        else
+        } else if constexpr (decltype(fxc)::value) {
+          asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr),
+                       "r"(__float2int_rn(__uint_as_float(wbits) * (float)xv))
+                       : "memory");
+        } else {
           asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
+        }
       };
       // item it: lane l loads posting l of each of its 4 blocks; da = byte
       // offset of the document inside a row, -1 when the lane has no posting
@@ -523,19 +589,19 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         return jj;
       };
       // NI loaded items of term jj: every entry of the term, every posting
-      auto score_items = [&](int jj, const int* da, const AccT* x, int ni) {
+      auto score_items = [&](auto fxc, int jj, const int* da, const AccT* x, int ni) {
         const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
         for (int32_t en = eb; en < ee; ++en) {
           const uint2 E = entry(en);
           const uint32_t row = acc_s + E.x;
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < 8; ++i)
-            if (i < 4 * ni && da[i] >= 0) red(row + (uint32_t)da[i], E.y, x[i]);
+            if (i < 4 * ni && da[i] >= 0) red(fxc, row + (uint32_t)da[i], E.y, x[i]);
         }
       };
       // 32 postings of the packed short segments: one posting per lane, its
       // own term and entries
-      auto score_packed = [&](int it) {
+      auto score_packed = [&](auto fxc, int it) {
         const int P = (it - total) * 32 + lane;
         if (P >= tiny_total) return;
         int jj = chunk_j0[it - total];
@@ -551,42 +617,46 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
         for (int32_t en = eb; en < ee; ++en) {
           const uint2 E = entry(en);
-          red(acc_s + E.x + da, E.y, xv);
+          red(fxc, acc_s + E.x + da, E.y, xv);
         }
       };
       // units are claimed two at a time; both items' postings are loaded
       // before either is scored, so that each warp keeps 256 postings in flight
-      int nxt = 0;
-      if (lane == 0) nxt = atomicAdd(&s_next, 2);
-      nxt = __shfl_sync(0xffffffffu, nxt, 0);
-      while (nxt < units) {
-        const int it = nxt;
+      auto run_units = [&](auto fxc) {
+        int nxt = 0;
         if (lane == 0) nxt = atomicAdd(&s_next, 2);
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
-        if (it + 1 < total) {
-          int da[8];
-          AccT x[8];
-          const int ja = load_item(it, da, x);
-          const int jb = load_item(it + 1, da + 4, x + 4);
-          if (ja == jb) {
-            score_items(ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
-          } else {
-            score_items(ja, da, x, 1);
-            score_items(jb, da + 4, x + 4, 1);
-          }
-        } else {
-          for (int u = it; u < min(it + 2, units); ++u) {
-            if (u < total) {
-              int da[4];
-              AccT x[4];
-              const int jj = load_item(u, da, x);
-              score_items(jj, da, x, 1);
+        while (nxt < units) {
+          const int it = nxt;
+          if (lane == 0) nxt = atomicAdd(&s_next, 2);
+          nxt = __shfl_sync(0xffffffffu, nxt, 0);
+          if (it + 1 < total) {
+            int da[8];
+            AccT x[8];
+            const int ja = load_item(it, da, x);
+            const int jb = load_item(it + 1, da + 4, x + 4);
+            if (ja == jb) {
+              score_items(fxc, ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
             } else {
-              score_packed(u);
+              score_items(fxc, ja, da, x, 1);
+              score_items(fxc, jb, da + 4, x + 4, 1);
+            }
+          } else {
+            for (int u = it; u < min(it + 2, units); ++u) {
+              if (u < total) {
+                int da[4];
+                AccT x[4];
+                const int jj = load_item(u, da, x);
+                score_items(fxc, jj, da, x, 1);
+              } else {
+                score_packed(fxc, u);
+              }
             }
           }
         }
-      }
+      };
+      if (fx) run_units(std::true_type{});
+      else run_units(std::false_type{});
       __syncthreads();
     }
 
@@ -663,8 +733,13 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               AccT* dst = acc + q * T + slab + 2 * dp;
               uint2 c = *reinterpret_cast<uint2*>(dst);
               AccT* v = reinterpret_cast<AccT*>(&c);
-              v[0] += r[i][0];
-              v[1] += r[i][1];
+              if constexpr (IMPACT == GS_IMPACT_U8) {
+                v[0] += r[i][0];
+                v[1] += r[i][1];
+              } else {
+                v[0] = tail_value(v[0], fx, s_isc[q]) + r[i][0];
+                v[1] = tail_value(v[1], fx, s_isc[q]) + r[i][1];
+              }
               *reinterpret_cast<uint2*>(dst) = c;
             }
           }
@@ -748,10 +823,11 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                 *reinterpret_cast<int4*>(dst) = v;
               } else {
                 float4 v = *reinterpret_cast<float4*>(dst);
-                v.x += d[0][2 * h + c];
-                v.y += d[1][2 * h + c];
-                v.z += d[2][2 * h + c];
-                v.w += d[3][2 * h + c];
+                const float isc = s_isc[q];
+                v.x = tail_value(v.x, fx, isc) + d[0][2 * h + c];
+                v.y = tail_value(v.y, fx, isc) + d[1][2 * h + c];
+                v.z = tail_value(v.z, fx, isc) + d[2][2 * h + c];
+                v.w = tail_value(v.w, fx, isc) + d[3][2 * h + c];
                 *reinterpret_cast<float4*>(dst) = v;
               }
             }
@@ -791,6 +867,11 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           }
         }
       }
+      __syncthreads();
+    } else if (fx) {
+      // no head: fixed-point rows become floats
+      float* af = reinterpret_cast<float*>(acc);
+      for (int i = threadIdx.x; i < gq * T; i += blockDim.x) af[i] = tail_value(af[i], true, s_isc[i / T]);
       __syncthreads();
     }
 
@@ -1046,7 +1127,8 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
     ks<<<((c.n_sample + ms - 1) / ms) * c.ng, kDtThreads, smem, s>>>(
         ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
         c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
-        p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, ms, c.n_sample);
+        p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, ms, c.n_sample,
+        p.fixp, p.qscale);
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
@@ -1064,7 +1146,8 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
   km<<<((c.nt + mm - 1) / mm) * c.ng, kDtThreads, smem, s>>>(
       ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
       c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
-      p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, mm, c.nt);
+      p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, mm, c.nt,
+      p.fixp, p.qscale);
   GS_LAUNCH_CHECK();
   record_stage(opts, 4, s);
   return GS_OK;
@@ -1132,7 +1215,7 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   record_stage(opts, 0, s);
   dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt,
                                        p.u_terms, p.u_ptr, p.n_u, p.ent, ix->head_slot, c.H, p.headw, p.head_act,
-                                       p.head_nact, flags);
+                                       p.head_nact, ix->max_abs, p.fixp, p.qscale, flags);
   GS_LAUNCH_CHECK();
   GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
   GS_CUDA_TRY(cudaMemsetAsync(p.tiebm, 0, sizeof(uint32_t) * (size_t)B * c.bm_words, s));

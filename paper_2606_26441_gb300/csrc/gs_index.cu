@@ -177,19 +177,21 @@ __device__ __forceinline__ float load_impact(const uint8_t* blk, int li) {
 template <int IMPACT>
 __global__ void finalize_kernel(const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block,
                                 const int32_t* __restrict__ term_len, int32_t V, int tile_docs,
-                                int num_tiles, float* __restrict__ max_score, uint32_t* __restrict__ seg,
-                                uint32_t* err) {
+                                int num_tiles, float* __restrict__ max_score, float* __restrict__ max_abs,
+                                uint32_t* __restrict__ seg, uint32_t* err) {
   const int t = blockIdx.x;
   constexpr int bb = block_bytes(IMPACT);
   const int64_t len = term_len[t];
   const uint8_t* base = blocks + term_block[t] * bb;
   uint32_t* srow = seg ? seg + (int64_t)t * (num_tiles + 1) : nullptr;
-  float mx = -INFINITY;
+  float mx = -INFINITY, ma = 0.0f;
   uint32_t e = 0;
   for (int64_t p = threadIdx.x; p < len; p += blockDim.x) {
     const uint8_t* blk = base + (p / kBlock) * bb;
     const int32_t doc = reinterpret_cast<const int32_t*>(blk)[p % kBlock];
-    mx = fmaxf(mx, load_impact<IMPACT>(blk, (int)(p % kBlock)));
+    const float xv = load_impact<IMPACT>(blk, (int)(p % kBlock));
+    mx = fmaxf(mx, xv);
+    ma = fmaxf(ma, fabsf(xv));
     int32_t prev = -1;
     if (p > 0) {
       const uint8_t* pb = base + ((p - 1) / kBlock) * bb;
@@ -206,16 +208,26 @@ __global__ void finalize_kernel(const uint8_t* __restrict__ blocks, const int64_
   }
   if (len == 0 && srow)
     for (int j = threadIdx.x; j <= num_tiles; j += blockDim.x) srow[j] = 0u;
-  // block max
-  __shared__ float red[32];
+  // block maxima
+  __shared__ float red[32], red_a[32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = mx;
+    red_a[threadIdx.x >> 5] = ma;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float m = -INFINITY;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+    float m = -INFINITY, a = 0.0f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      m = fmaxf(m, red[i]);
+      a = fmaxf(a, red_a[i]);
+    }
     max_score[t] = len > 0 ? m : 0.0f;
+    max_abs[t] = a;
   }
   if (e) atomicOr(err, e);
 }
@@ -276,10 +288,10 @@ void launch_scatter(const int64_t* indptr, const int32_t* terms, const float* w,
 
 template <int IMPACT>
 void launch_finalize(const uint8_t* blocks, const int64_t* term_block, const int32_t* term_len, int32_t V,
-                     int tile_docs, int num_tiles, float* max_score, uint32_t* seg, uint32_t* err,
-                     cudaStream_t s) {
+                     int tile_docs, int num_tiles, float* max_score, float* max_abs, uint32_t* seg,
+                     uint32_t* err, cudaStream_t s) {
   finalize_kernel<IMPACT><<<V, 256, 0, s>>>(blocks, term_block, term_len, V, tile_docs, num_tiles,
-                                            max_score, seg, err);
+                                            max_score, max_abs, seg, err);
 }
 
 }  // namespace
@@ -293,6 +305,7 @@ static void free_index(gs_index* ix) {
   cudaFree(ix->term_block);
   cudaFree(ix->term_len);
   cudaFree(ix->max_score);
+  cudaFree(ix->max_abs);
   cudaFree(ix->seg);
   cudaFree(ix->head_term);
   cudaFree(ix->head_slot);
@@ -370,6 +383,7 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
   if ((e = cudaMalloc(&nblkb.p, sizeof(int64_t) * vocab)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMalloc(&ix->term_block, sizeof(int64_t) * (vocab + 1))) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMalloc(&ix->max_score, sizeof(float) * vocab)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMalloc(&ix->max_abs, sizeof(float) * vocab)) != cudaSuccess) return cuda_fail(e);
   if (nnz > 0)
     count_kernel<<<grid_for(num_docs, 256, sms), 256, 0, s>>>(doc_indptr, doc_terms, num_docs, vocab, dpc, cnt);
   // 3. per-(chunk, term) bases, list lengths
@@ -424,23 +438,23 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
     if ((e = cudaMalloc(&ix->seg, seg_bytes)) != cudaSuccess) return cuda_fail(e);
     ix->meta_bytes += (int64_t)seg_bytes;
   }
-  ix->meta_bytes += (int64_t)vocab * (8 + 4 + 4) + 8;
+  ix->meta_bytes += (int64_t)vocab * (8 + 4 + 4 + 4) + 8;
   switch (impact) {
     case GS_IMPACT_F32:
       launch_finalize<GS_IMPACT_F32>(ix->blocks, ix->term_block, ix->term_len, vocab, ix->tile_docs, ix->num_tiles,
-                                     ix->max_score, ix->seg, err, s);
+                                     ix->max_score, ix->max_abs, ix->seg, err, s);
       break;
     case GS_IMPACT_F16:
       launch_finalize<GS_IMPACT_F16>(ix->blocks, ix->term_block, ix->term_len, vocab, ix->tile_docs, ix->num_tiles,
-                                     ix->max_score, ix->seg, err, s);
+                                     ix->max_score, ix->max_abs, ix->seg, err, s);
       break;
     case GS_IMPACT_BF16:
       launch_finalize<GS_IMPACT_BF16>(ix->blocks, ix->term_block, ix->term_len, vocab, ix->tile_docs,
-                                      ix->num_tiles, ix->max_score, ix->seg, err, s);
+                                      ix->num_tiles, ix->max_score, ix->max_abs, ix->seg, err, s);
       break;
     default:
       launch_finalize<GS_IMPACT_U8>(ix->blocks, ix->term_block, ix->term_len, vocab, ix->tile_docs, ix->num_tiles,
-                                    ix->max_score, ix->seg, err, s);
+                                    ix->max_score, ix->max_abs, ix->seg, err, s);
       break;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);

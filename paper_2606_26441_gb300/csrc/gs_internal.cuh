@@ -44,6 +44,7 @@ struct gs_index {
   int64_t* term_block = nullptr;   // V + 1
   int32_t* term_len = nullptr;     // V
   float* max_score = nullptr;      // V
+  float* max_abs = nullptr;        // V: largest |stored impact| of each list
   uint32_t* seg = nullptr;         // V * (num_tiles + 1)
   // dense head: the H longest lists as an [H][head_ld] impact matrix
   int32_t head_H = 0;

@@ -284,6 +284,28 @@ def test_doc_tiled_large_query_groups():
         c.idx.free()
 
 
+def test_fixed_point_tail_coarse_scale():
+    """Float impacts accumulate the sparse tail in fixed point with a per-query
+    scale 2^S chosen from sum |w| max|x|.  One heavy tail term and three tiny
+    ones give a coarse scale (S near 22) while the top-1000 reaches documents
+    that hold only the tiny terms (A ~ 1e-4): scores stay within tau there."""
+    docs = synth.docs(40_000, seed=9)
+    df = np.bincount(docs.terms, minlength=docs.vocab)
+    order = np.argsort(-df, kind="stable")
+    heavy, tiny = int(order[150]), [int(t) for t in order[200:203]]  # outside any dense head
+    rows = [([heavy] + tiny, [90.0, 1e-4, 2e-4, 3e-4]), (tiny, [1e-4, 1e-4, 1e-4])]
+    base = synth.queries(14, seed=9)
+    rows += [tuple(map(list, base.row(i))) for i in range(14)]
+    indptr = np.cumsum([0] + [len(r[0]) for r in rows]).astype(np.int64)
+    qs = synth.SparseBatch(indptr, np.array(sum([list(r[0]) for r in rows], []), np.int32),
+                           np.array(sum([list(r[1]) for r in rows], []), np.float32))
+    for impact in ("f32", "f16"):
+        c = Case(docs, qs, impact)
+        for k in (10, 1000):
+            c.check(k, "doc_tiled")
+        c.idx.free()
+
+
 def test_bad_query_terms_are_flagged():
     gs = _gs()
     docs = synth.docs(3_000, seed=4)
