@@ -113,7 +113,7 @@ typedef struct {
   int32_t head_terms; /* dense head: the H terms with the longest posting
                          lists also get a dense [H x N] impact matrix that the
                          doc-tiled kernel multiplies (FMAs or tensor-core
-                         MMAs) instead of scattering them; 0 = default (32
+                         MMAs) instead of scattering them; 0 = default (24
                          for FP32 impacts, 64 otherwise), -1 = none, at most
                          GS_MAX_HEAD_TERMS */
   int32_t doc_major;  /* 1: also keep a document-major copy (doc CSR of stored

@@ -113,7 +113,7 @@ def test_dense_head_layout(cases):
         c = cases[impact]
         st = c.idx.stats()
         lay = c.idx.layout()
-        assert st.head_terms == {"f32": 32, "u8": 64}[impact]  # defaults: FMA head 32 rows, tensor head 64
+        assert st.head_terms == {"f32": 24, "u8": 64}[impact]  # defaults: FMA head 24 rows, tensor head 64
         H, ld = st.head_terms, lay.head_ld
         ib = {"f32": 4, "u8": 1}[impact]
         torch.cuda.synchronize()
