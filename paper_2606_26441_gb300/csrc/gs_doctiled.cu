@@ -497,10 +497,11 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       // the tile's head rows are prefetched into L2 now so that they are
       // resident when the head phase reads them
       const int ib = impact_bytes(IMPACT);
-      const int lines_per_row = (T * ib + 127) / 128;
-      for (int i = threadIdx.x; i < nact * lines_per_row; i += blockDim.x) {
-        const uint8_t* ptr = head_dense + ((int64_t)s_hact[i / lines_per_row] * head_ld + doc0) * ib +
-                             (int64_t)(i % lines_per_row) * 128;
+      // 128-byte lines per row: T ib / 128, a power of two (T >= 256)
+      const int lpr_log2 = __ffs((T * ib) >> 7) - 1;
+      for (int i = threadIdx.x; i < (nact << lpr_log2); i += blockDim.x) {
+        const uint8_t* ptr = head_dense + ((int64_t)s_hact[i >> lpr_log2] * head_ld + doc0) * ib +
+                             (int64_t)(i & ((1 << lpr_log2) - 1)) * 128;
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
       }
     }
@@ -898,40 +899,45 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       const uint32_t th = s_theta[ql];
       const AccT* row = acc + ql * T;
       for (int w0 = 0; w0 < T; w0 += 1024) {
-        uint32_t gt_bits = 0, eq_bits = 0;
+        // one compare per document (score >= theta_q); the few hits are then
+        // split into candidates (> theta_q) and ties (== theta_q)
+        uint32_t ge_bits = 0;
         const int nc = min(8, (T - w0) / 128);
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 8; ++c) {
           if (c >= nc) break;
           const int d0 = w0 + c * 128 + lane * 4;
           const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
           const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < 4; ++i) {
-            bool gt, eq;
-            if (R <= 0) {
-              gt = true;
-              eq = false;
-            } else if (IMPACT == GS_IMPACT_U8) {
-              gt = (int32_t)rv[i] > (int32_t)th;
-              eq = (int32_t)rv[i] == (int32_t)th;
-            } else {
-              gt = __uint_as_float(rv[i]) > __uint_as_float(th);
-              eq = __uint_as_float(rv[i]) == __uint_as_float(th);
-            }
-            gt_bits |= (uint32_t)gt << (4 * c + i);
-            eq_bits |= (uint32_t)eq << (4 * c + i);
+            bool ge;
+            if (IMPACT == GS_IMPACT_U8) ge = (int32_t)rv[i] >= (int32_t)th;
+            else ge = __uint_as_float(rv[i]) >= __uint_as_float(th);
+            ge_bits |= (uint32_t)(ge || R <= 0) << (4 * c + i);
           }
         }
         if (n_in < (int64_t)(w0 + 1024)) {
           // the collection ends inside this window: drop documents >= N
           uint32_t keep = 0;
-  #pragma unroll
+#pragma unroll
           for (int c = 0; c < 8; ++c)
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
-          gt_bits &= keep;
-          eq_bits &= keep;
+          ge_bits &= keep;
+        }
+        uint32_t gt_bits = ge_bits, eq_bits = 0;
+        if (R > 0) {
+          gt_bits = 0;
+          for (uint32_t rem = ge_bits; rem; rem &= rem - 1) {
+            const int bit = __ffs(rem) - 1;
+            const AccT v = row[w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3)];
+            bool gt;
+            if (IMPACT == GS_IMPACT_U8) gt = (int32_t)v > (int32_t)th;
+            else gt = v > __uint_as_float(th);
+            if (gt) gt_bits |= 1u << bit;
+            else eq_bits |= 1u << bit;
+          }
         }
         const int n_gt = __popc(gt_bits);
         int incl = n_gt;
