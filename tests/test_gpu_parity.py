@@ -268,20 +268,23 @@ def test_u8_head_with_large_summed_weights():
 def test_doc_tiled_large_query_groups():
     """Groups with more distinct terms than one planning batch holds and more
     (query, weight) entries than shared memory stages: the kernel plans the
-    group in several batches per tile and reads entries from global memory."""
+    group in several batches per tile and reads entries from global memory,
+    with float and with fixed-point tail reductions."""
     docs = synth.docs(30_000, seed=8)
     rng = np.random.default_rng(8)
-    n, per = 20, 150
-    terms = np.concatenate([rng.choice(docs.vocab, size=per, replace=False) for _ in range(n)]).astype(np.int32)
-    weights = rng.uniform(0.05, 3.0, size=n * per).astype(np.float32)
-    indptr = np.arange(0, n * per + 1, per, dtype=np.int64)
-    qs = synth.SparseBatch(indptr, terms, weights)
-    for impact in ("u8", "f32", "f16"):
-        c = Case(docs, qs, impact)
-        for kw in ({}, {"use_head": -1}, {"use_head": 1}, {"use_head": 2}):
-            for k in (10, 1000):
-                c.check(k, "doc_tiled", **kw)
-        c.idx.free()
+    # large weights: the float tail falls back to float reductions; small weights
+    # (sum |w| max|x| ~ 5 per query): the fixed-point tail with unstaged entries
+    for n, per, wlo, whi in ((20, 150, 0.05, 3.0), (18, 100, 0.005, 0.02)):
+        terms = np.concatenate([rng.choice(docs.vocab, size=per, replace=False) for _ in range(n)]).astype(np.int32)
+        weights = rng.uniform(wlo, whi, size=n * per).astype(np.float32)
+        indptr = np.arange(0, n * per + 1, per, dtype=np.int64)
+        qs = synth.SparseBatch(indptr, terms, weights)
+        for impact in ("u8", "f32", "f16"):
+            c = Case(docs, qs, impact)
+            for kw in ({}, {"use_head": -1}, {"use_head": 1}, {"use_head": 2}):
+                for k in (10, 1000):
+                    c.check(k, "doc_tiled", **kw)
+            c.idx.free()
 
 
 def test_fixed_point_tail_coarse_scale():
