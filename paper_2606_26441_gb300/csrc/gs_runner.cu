@@ -76,9 +76,11 @@ std::vector<gs_search_opts> candidates(const gs_index* ix, const gs_search_opts&
   for (int T = T0; T <= 4096; T *= 2) {
     for (int G : {4, 8, 16}) {
       if ((int64_t)G * T > 16384) continue;
-      if (G > bucket && G != 4) continue;
       for (int head : {0, -1}) {
         if (head == 0 && (G != 16 || ix->head_H == 0)) continue;
+        // groups larger than the bucket only for the dense head (its group is
+        // fixed at 16 queries, and it can pay even half-filled)
+        if (G > bucket && G != 4 && head != 0) continue;
         for (int R : {32, 64, 128}) {
           gs_search_opts o = base;
           o.algo = GS_ALGO_DOC_TILED;
