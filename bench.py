@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -69,11 +70,15 @@ KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_to
 
 
 def kernel_source_digest():
-    """sha256 over the doc-tiled kernel's source files (in KERNEL_SOURCES order)."""
+    """sha256 over the doc-tiled kernel's source files (in KERNEL_SOURCES order), with
+    comments and whitespace removed: a digest of the code, not of its comments."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2606_26441_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2606_26441_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -3,24 +3,27 @@
 // shared-memory accumulation), designed for sm_103a.
 //
 // The queries of a batch form groups of G consecutive queries; the documents
-// form tiles of T consecutive ids.  One CTA owns a (group, tile) pair and keeps
-// the G x T block of score rows in shared memory.  For every distinct term of
-// the group it reads the segment of the term's posting list that falls inside
-// the tile (the segment table of the index gives its bounds, lists being
-// doc-sorted, Sec. 3.2) once, 32 postings per warp step, and adds w * x into
-// the rows of every query of the group holding the term (shared-memory
-// reductions, no global atomics).  Padding (doc -1) lies outside every
-// segment.
+// form tiles of T consecutive ids.  A CTA owns one group and a run of tiles and
+// keeps the G x T block of score rows of its current tile in shared memory.
+// Sparse tail: for every distinct term of the group outside the dense head it
+// reads the segment of the term's posting list that falls inside the tile (the
+// segment table of the index gives its bounds, lists being doc-sorted, Sec. 3.2)
+// once, 32 postings per warp step, and adds w * x into the rows of every query
+// of the group holding the term (shared-memory reductions, no global atomics;
+// integer reductions in fixed point where a bound on the tail score allows).
+// Padding (doc -1) lies outside every segment.  Dense head: the most frequent
+// terms' rows are multiplied densely (CUDA-core FMAs or tensor-core MMAs).
 //
 // Exact top-k without dense rows: every R-th full tile is a sample tile.  The
 // sample tiles are scored first and written out; theta_q, the k-th largest
-// sample score of query q rounded down to 22 key bits, is a lower bound of
-// its k-th largest score over all documents.  The remaining tiles are then scored, and every document
-// with score > theta_q is appended to a per-query candidate list; documents
-// equal to theta_q set a bit in a per-query tie bitmap.  A final kernel per
-// query returns the top-k of the candidates by (score desc, id asc), taking
-// the lowest-id ties when fewer than k candidates exceed theta_q.  Every
-// document's score is computed exactly once, so the bound holds exactly.
+// sample score of query q (rounded down to 22 key bits for float scores), is a
+// lower bound of its k-th largest score over all documents.  The remaining
+// tiles are then scored, and every document with score > theta_q is appended
+// to a per-query candidate list; documents equal to theta_q set a bit in a
+// per-query tie bitmap.  A final kernel per query returns the top-k of the
+// candidates by (score desc, id asc), taking the lowest-id ties when fewer
+// than k candidates exceed theta_q.  Every document's score is computed
+// exactly once, so the bound holds exactly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,8 +36,8 @@
 namespace gs {
 namespace {
 
-constexpr int kDtThreads = 512;                  // two CTAs per SM (64 registers each)
-constexpr int kDtMaxAccBytes = 64 * 1024;     // G x T accumulators
+constexpr int kDtThreads = 512;              // two CTAs per SM (64 registers each)
+constexpr int kDtMaxAccBytes = 64 * 1024;    // G x T accumulators
 constexpr int kEntCap = 1280;                // query entries staged in shared memory (10 KB)
 constexpr int kItemCap = 4608;               // (term, 128-posting chunk) items per term batch (9 KB)
 constexpr int kTinySeg = 32;                 // segments shorter than this are packed, not itemised
@@ -575,7 +578,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
         const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
         const uint32_t len = (uint32_t)s_len[jj];
-  #pragma unroll
+#pragma unroll
         for (int i = 0; i < 4; ++i) {
           da[i] = -1;
           x[i] = (AccT)0;
@@ -678,7 +681,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
           const int64_t col = doc0 + slab + 2 * dp;
           AccT r[16][2];
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
           auto load2 = [&](int a, AccT& x0, AccT& x1) {
             const int64_t at = (int64_t)s_hact[a] * head_ld + col;
@@ -701,20 +704,20 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           };
           for (int a0 = 0; a0 < nact; a0 += 4) {
             AccT xs[4][2];
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 4; ++u) {
               xs[u][0] = xs[u][1] = (AccT)0;
               if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
             }
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (a0 + u >= nact) break;
               const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
-  #pragma unroll
+#pragma unroll
               for (int q4 = 0; q4 < 4; ++q4) {
                 AccT w4[4];
                 *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
-  #pragma unroll
+#pragma unroll
                 for (int v = 0; v < 4; ++v) {
                   if (IMPACT == GS_IMPACT_U8) {
                     r[4 * q4 + v][0] += w4[v] * xs[u][0];
@@ -727,7 +730,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               }
             }
           }
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int q = 16 * qh + i;
             if (q < gq) {
@@ -941,7 +944,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         }
         const int n_gt = __popc(gt_bits);
         int incl = n_gt;
-  #pragma unroll
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int y = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += y;
