@@ -65,6 +65,7 @@ def cores() -> int:
         return os.cpu_count() or 1
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_dt_tile_kernel_docs8.8m_b500_top1000.md")
 KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh")
 
@@ -229,6 +230,12 @@ def workload_config(w, impact, algo):
 
 
 # --------------------------------------------------------------------------- GPU arm
+
+def naive_stream_bytes(docs, qs, impact, df):
+    """Every query reading its own terms' posting lists, plus FP32 score rows written once
+    and read once (8 B per query and document)."""
+    return int(df[qs.terms].sum()) * (4 + BYTES_PER_IMPACT[impact]) + 8 * qs.n * docs.n
+
 
 def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
     """Algorithmic bytes of the dominant kernel per launch.
@@ -413,6 +420,8 @@ def run_gpu(args, w, docs, qs, world, rank, local):
                      "traffic": recorded_traffic(w.name, args.headline), "algorithmic_bytes": alg_bytes,
                      "kernel_ms": kern_ms,
                      "postings_read": extra["postings"], "scatter_updates": updates,
+                     "naive_stream_bytes": naive_stream_bytes(docs, qs, head_imp, df),
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "updates_per_s": updates / (kern_ms / 1e3)},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
@@ -638,9 +647,15 @@ def main():
         t = time.perf_counter()
         ref.topk(sub.indptr, sub.terms, sub.weights, w.k, threads=c)
         dt = time.perf_counter() - t
+        # one query on one thread: the oracle's per-query cost without parallelism
+        one = qs.slice(0, 1)
+        t1 = time.perf_counter()
+        ref.topk(one.indptr, one.terms, one.weights, w.k, threads=1)
+        dt1 = time.perf_counter() - t1
         out["cpu_baseline"] = {"value": nq / dt, "unit": "QPS", "cores": c, "kind": "oracle",
                                "sample": f"first {nq} of the {w.batch} queries over the full {w.n_docs}-doc "
-                                         f"collection ({dt:.1f}s wall on {c} threads)"}
+                                         f"collection ({dt:.1f}s wall on {c} threads)",
+                               "single_thread_ms_per_query": dt1 * 1e3}
     out["setup_s"] = {"generate": gen_s}
     if rank == 0:
         print(json.dumps(out), flush=True)
