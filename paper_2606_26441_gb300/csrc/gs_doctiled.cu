@@ -675,10 +675,9 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         // flight, the weights are warp-wide broadcasts, and every (query,
         // document) cell has one owner (no atomics)
         constexpr int kSlab = 2 * kDtThreads;
-        const int qh = 0;
         const int dp = warp * 32 + lane;
         for (int slab = 0; slab < T; slab += kSlab) {
-          if (slab + 2 * dp >= T) break;  // tiles shorter than 1024 documents
+          if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
           const int64_t col = doc0 + slab + 2 * dp;
           AccT r[16][2];
 #pragma unroll
@@ -712,7 +711,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (a0 + u >= nact) break;
-              const AccT* wr = s_w + (a0 + u) * kHeadG + 16 * qh;
+              const AccT* wr = s_w + (a0 + u) * kHeadG;
 #pragma unroll
               for (int q4 = 0; q4 < 4; ++q4) {
                 AccT w4[4];
@@ -732,7 +731,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int q = 16 * qh + i;
+            const int q = i;
             if (q < gq) {
               AccT* dst = acc + q * T + slab + 2 * dp;
               uint2 c = *reinterpret_cast<uint2*>(dst);
