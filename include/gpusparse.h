@@ -226,6 +226,9 @@ gs_status gs_search_workspace_size(const gs_index* index, int32_t batch, int64_t
  * Outputs on the device, row-major [batch x k]:
  *   out_ids    int32 document ids, ordered by (score desc, id asc);
  *   out_scores float32 scores (int32 on the U8 path).
+ * Scores are those of Eq. 4 over the stored impacts: exact on the U8 path;
+ * on float paths within 1e-5 * sum |w x| + 1e-6 of the exact value, the
+ * order taken by the returned scores.
  * 1 <= k <= min(N, GS_MAX_K).  workspace: device, >= the size reported by
  * gs_search_workspace_size for the same arguments, 256-byte aligned; it is
  * used as scratch and must not be shared by calls that overlap on the GPU.
