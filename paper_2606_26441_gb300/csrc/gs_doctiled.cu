@@ -339,14 +339,17 @@ __device__ __forceinline__ float tail_value(float v, bool fx, float isc) {
   return fx ? (float)__float_as_int(v) * isc : v;
 }
 
-// One CTA per (tile, group): G x T score block in shared memory.
+// One CTA per (query group, run of tiles_per_cta tiles); per tile a G x T
+// score block in shared memory, filled by the sparse tail, the dense head and
+// read by the candidate epilogue (sample mode: written to the sample rows).
 //
-// Work items are (term, chunk of 4 posting blocks = 128 postings) pairs of
-// the group's distinct terms, handed out dynamically to the 32 warps.  Lane l
-// of a warp takes posting l of each of the 4 blocks, so the 32 lanes of one
-// reduction address 32 distinct documents of one query row (consecutive
-// documents for dense terms: no bank conflicts), and every loaded posting
-// serves all of the group's queries holding the term.
+// Tail work items are (term, chunk of 4 posting blocks = 128 postings) pairs
+// of the group's distinct terms, handed out dynamically to the 16 warps, two
+// at a time.  Lane l of a warp takes posting l of each of the 4 blocks, so the
+// 32 lanes of one reduction address 32 distinct documents of one query row
+// (consecutive documents for dense terms: few bank conflicts), and every
+// loaded posting serves all of the group's queries holding the term.
+// Segments shorter than kTinySeg are packed 32 postings per warp step.
 template <int IMPACT, int MODE, int HK>
 __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const uint32_t* __restrict__ seg,
