@@ -420,6 +420,35 @@ def test_reduced_precision_error_vs_fp64():
         assert by[impact][3] >= 0.8, by[impact]
 
 
+@pytest.mark.slow
+def test_full_size_batch_sampled_rows():
+    """The bench's workload and launch: 8,841,823 documents, one batch of 500
+    queries, top-1000, default doc-tiled plan.  The oracle checks a sample of the
+    returned rows (every 32nd query: one per query group), uint8 bit-exact and
+    FP32 / FP16 within tau."""
+    import os
+    docs = synth.docs(synth.N_8_8M, seed=0, threads=os.cpu_count() or 0)
+    qs = synth.queries(500, seed=0)
+    k = 1000
+    rows = np.arange(0, qs.n, 32)
+    parts = [qs.slice(int(r), int(r) + 1) for r in rows]
+    indptr = np.cumsum([0] + [p.nnz for p in parts]).astype(np.int64)
+    sample = synth.SparseBatch(indptr, np.concatenate([p.terms for p in parts]),
+                               np.concatenate([p.weights for p in parts]))
+    for impact in ("u8", "f32", "f16"):
+        c = Case(docs, qs, impact)
+        ids, sc, flags = c.search(k, "doc_tiled")
+        assert flags == 0
+        c.idx.free()
+        rid, rsc, _ = c.ref.topk(sample.indptr, sample.terms, sample.weights, k)
+        if impact == "u8":
+            check.check_u8(ids[rows], sc[rows], rid, rsc)
+        else:
+            check.check_float(c.ref, sample.indptr, sample.terms, sample.weights, ids[rows], sc[rows], rid, rsc,
+                              docs.n)
+        del c
+
+
 def test_runner_graph_replay_matches_search():
     """Uneven batches through captured graphs (autotuned plans) equal the direct search."""
     gs = _gs()
