@@ -181,7 +181,12 @@ def _stream(stream):
 
 def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0, use_head=0,
               stage_events=None) -> gs_search_opts:
-    """stage_events: None or GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
+    """gs_search_opts (0 = the library's default for each field).
+
+    algo: "auto", "term_parallel", "doc_tiled" or "doc_parallel"; use_head: 0 = auto (FMA head
+    for FP32 impacts, tensor-core head otherwise), 1 = FMA head, 2 = tensor-core head, -1 = none;
+    sample_stride 1 = no sample (every document a candidate).  stage_events: None or
+    GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
     o = gs_search_opts()
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.group_queries, o.tile_docs = group_queries, tile_docs
@@ -283,7 +288,9 @@ class Index:
 
 def gs_index_build(doc_indptr, doc_terms, doc_w, vocab: int, impact: str = "f32", tile_docs: int = 0,
                    head_terms: int = 0, doc_major: bool = False, stream=None) -> Index:
-    """Builds the index from device CSR tensors (int64 indptr, int32 terms, float32 weights)."""
+    """Builds the index from device CSR tensors (int64 indptr, int32 terms, float32 weights).
+
+    head_terms: 0 = default (24 for FP32 impacts, 64 otherwise), -1 = no dense head."""
     L = load()
     assert doc_indptr.dtype == torch.int64 and doc_terms.dtype == torch.int32 and doc_w.dtype == torch.float32
     h = ctypes.c_void_p()
