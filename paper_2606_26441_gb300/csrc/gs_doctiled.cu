@@ -499,18 +499,6 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       uint4* a4 = reinterpret_cast<uint4*>(acc);
       for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
     }
-    if (HEAD) {
-      // the tile's head rows are prefetched into L2 now so that they are
-      // resident when the head phase reads them
-      const int ib = impact_bytes(IMPACT);
-      // 128-byte lines per row: T ib / 128, a power of two (T >= 256)
-      const int lpr_log2 = __ffs((T * ib) >> 7) - 1;
-      for (int i = threadIdx.x; i < (nact << lpr_log2); i += blockDim.x) {
-        const uint8_t* ptr = head_dense + ((int64_t)s_hact[i >> lpr_log2] * head_ld + doc0) * ib +
-                             (int64_t)(i & ((1 << lpr_log2) - 1)) * 128;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-      }
-    }
     __syncthreads();
 
     for (int j0 = 0; j0 < nterm; j0 += tb) {
