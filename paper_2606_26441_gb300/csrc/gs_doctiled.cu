@@ -499,7 +499,9 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       uint4* a4 = reinterpret_cast<uint4*>(acc);
       for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
     }
-    __syncthreads();
+    // the planning scan's barriers order the clearing before the tail's
+    // reductions; a group without tail terms needs one before the head
+    if (nterm == 0) __syncthreads();
 
     for (int j0 = 0; j0 < nterm; j0 += tb) {
       const int j = j0 + threadIdx.x;
