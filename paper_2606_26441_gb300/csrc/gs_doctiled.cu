@@ -981,11 +981,12 @@ __global__ void dt_sample_emit_kernel(const uint32_t* __restrict__ samp, int64_t
   const int lane = threadIdx.x & 31;
   const uint32_t theta = theta_key<ST>(theta_bits, q, R);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int t_log2 = __ffs(T) - 1;  // T is a power of two
   // uniform per warp: chunks of 32 consecutive sample positions
   for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < sample_docs; i0 += stride) {
     const int64_t i = i0 + lane;
-    const int64_t st = i / T;
-    const int64_t doc = st * R * T + (i - st * T);
+    const int64_t st = i >> t_log2;  // sample tile st is tile st R
+    const int64_t doc = ((st * R) << t_log2) + (i & (int64_t)(T - 1));
     const uint32_t raw = samp[(int64_t)q * sample_docs + i];
     ST v;
     memcpy(&v, &raw, 4);
