@@ -1122,7 +1122,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
   const int sms = ix->sms > 0 ? ix->sms : 1;
   auto per_cta = [&](int n_tiles) {
     const int64_t items = (int64_t)n_tiles * c.ng;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(8, items / (2 * (int64_t)sms * 16)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, items / (2 * (int64_t)sms * 16)));
   };
   if (c.R > 0) {
     const int ms = per_cta(c.n_sample);
