@@ -96,9 +96,12 @@ typedef enum {
 /* flag bits of the workspace flag word */
 #define GS_FLAG_BAD_TERM 1u     /* a query term id outside [0, V) was skipped */
 #define GS_FLAG_BAD_WEIGHT 2u   /* a non-finite query weight was skipped */
-#define GS_FLAG_CAND_OVERFLOW 4u/* doc-tiled: a candidate list overflowed and
-                                   the row was recomputed on the dense path */
-#define GS_FLAG_TIMEOUT 8u      /* a bounded device wait gave up */
+#define GS_FLAG_CAND_OVERFLOW 4u/* doc-tiled, informational: more documents beat
+                                   a query's sampled threshold than its
+                                   candidate list holds; that query's top-k
+                                   was recomputed exactly (radix select of
+                                   its k-th score over fresh scores of every
+                                   document), so the results stay exact */
 #define GS_FLAG_BAD_INDPTR 16u  /* the query CSR row pointer was not monotone
                                    or ended past q_nnz: results undefined */
 

@@ -110,7 +110,16 @@ struct DtPlan {
   uint32_t* samp;     // [B][sample_docs]
   uint32_t* theta;    // [B] lower bound of the k-th largest sample score (raw bits)
   uint2* cand;        // [B][cap] (key, doc)
-  uint32_t* cand_cnt; // [B]
+  uint32_t* cand_cnt; // [B]; the cleared block [B cand_cnt][B q_over][ng g_mark][n_groups]
+  uint32_t* q_over;   // [B] 1: the query's candidate list overflowed
+  uint32_t* g_mark;   // [ng] 1: the group is on the recovery list
+  uint32_t* n_ovg;    // groups on the recovery list
+  int32_t* ov_groups; // [ng] the recovery list
+  uint32_t* ov_prefix;// [B] resolved key bits of the exact k-th score
+  int32_t* ov_need;   // [B] documents at the current prefix still to take
+  uint32_t* ov_theta; // [B] the exact k-th score (raw bits)
+  uint32_t* ov_hist;  // [B][2048] digit histogram
+  size_t zero_bytes;  // bytes of the cleared block
   uint32_t* tiebm;    // [B][bm_words]
   uint32_t* headw;    // [ng][H][kHeadG] head weights (float or int bits)
   int32_t* head_act;  // [ng][H] head rows with a non-zero weight
@@ -130,7 +139,16 @@ DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const
   p.samp = cv.take<uint32_t>((size_t)B * std::max<int64_t>(c.sample_docs, 1));
   p.theta = cv.take<uint32_t>(B);
   p.cand = cv.take<uint2>((size_t)B * c.cap);
-  p.cand_cnt = cv.take<uint32_t>(B);
+  p.zero_bytes = sizeof(uint32_t) * (2 * (size_t)B + c.ng + 1);
+  p.cand_cnt = cv.take<uint32_t>(2 * (size_t)B + c.ng + 1);
+  p.q_over = p.cand_cnt ? p.cand_cnt + B : nullptr;
+  p.g_mark = p.cand_cnt ? p.q_over + B : nullptr;
+  p.n_ovg = p.cand_cnt ? p.g_mark + c.ng : nullptr;
+  p.ov_groups = cv.take<int32_t>(c.ng);
+  p.ov_prefix = cv.take<uint32_t>(B);
+  p.ov_need = cv.take<int32_t>(B);
+  p.ov_theta = cv.take<uint32_t>(B);
+  p.ov_hist = cv.take<uint32_t>((size_t)B * 2048);
   p.tiebm = cv.take<uint32_t>((size_t)B * c.bm_words);
   p.headw = cv.take<uint32_t>((size_t)c.ng * std::max(c.H, 1) * kHeadG);
   p.head_act = cv.take<int32_t>((size_t)c.ng * std::max(c.H, 1));
@@ -284,7 +302,22 @@ __device__ __forceinline__ float load_x(const uint8_t* blk, int lane) {
   return (float)__ldg(blk + 128 + lane);
 }
 
-enum { kModeSample = 0, kModeMain = 1 };
+// Passes of the tile kernel: the sample tiles, the other tiles (candidates
+// above the sampled threshold), and the recovery passes of queries whose
+// candidate list overflowed (a persistent grid over their groups, every tile;
+// see dt_search).
+enum { kModeSample = 0, kModeMain = 1, kModeRecover = 2 };
+
+// State of the exact recovery of overflowed queries (device workspace).
+struct DtRecover {
+  const int32_t* groups;     // [ng] groups holding an overflowed query
+  const uint32_t* n_groups;  // how many
+  const uint32_t* q_over;    // [B] 1: the query's top-k is recomputed
+  uint32_t* hist;            // [B][2048] digit histogram of the current pass
+  const uint32_t* prefix;    // [B] key bits resolved by the earlier passes
+  const uint32_t* theta;     // [B] the exact k-th score (raw bits), emission pass
+  int pass;                  // 0..2: histogram of key digit `pass`; 3: emission
+};
 
 // theta_q: key of the k-th largest sample score (stored as raw score bits)
 template <typename AccT>
@@ -361,14 +394,19 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
     const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
     const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles,
-    const int32_t* __restrict__ fixp, const int32_t* __restrict__ qscale) {
+    const int32_t* __restrict__ fixp, const int32_t* __restrict__ qscale, DtRecover rec) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
   constexpr bool HEAD = HK != kHeadNone;
+  // Recovery passes must score every document identically in each of their
+  // four passes: float tails then accumulate exact int64 fixed-point sums
+  // (order-independent), integer tails are exact already.
+  constexpr bool REC64 = MODE == kModeRecover && IMPACT != GS_IMPACT_U8;
+  constexpr int kCell = REC64 ? 8 : 4;  // bytes per tail accumulator
   // dynamic shared memory: [G x T accumulators][staged query entries][item -> term]
   extern __shared__ __align__(16) uint8_t dyn_smem[];
   AccT* acc = reinterpret_cast<AccT*>(dyn_smem);
-  uint2* ent_s = reinterpret_cast<uint2*>(dyn_smem + (size_t)G * T * sizeof(AccT));
+  uint2* ent_s = reinterpret_cast<uint2*>(dyn_smem + (size_t)G * T * kCell);
   uint16_t* item_term = reinterpret_cast<uint16_t*>(ent_s + kEntCap);
   uint16_t* chunk_j0 = item_term + kItemCap;
   __shared__ const uint8_t* s_p0[kDtThreads];  // first block of the term's segment
@@ -378,6 +416,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int32_t s_tp[kDtThreads + 1];     // packed position of each short segment
   __shared__ int32_t s_e0[kDtThreads + 1];  // entries of term j: [s_e0[j], s_e0[j + 1])
   __shared__ uint32_t s_theta[kMaxGroup];
+  __shared__ uint32_t s_over[MODE == kModeRecover ? kMaxGroup : 1];
   __shared__ float s_sc[kMaxGroup], s_isc[kMaxGroup];  // fixed-point tail: 2^S_q and 2^-S_q
   __shared__ int warp_buf[32];
   __shared__ int s_next;
@@ -391,579 +430,666 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int32_t s_t[kDtThreads];   // the group's terms (one batch)
   __shared__ int32_t s_tb[kDtThreads];  // and their first index blocks
 
-  // the CTA scores tiles [tile_begin, tile_end) of query group g; the
-  // group's data are read once and serve all of them
-  const int g = blockIdx.x % ng;
-  const int tile_begin = (blockIdx.x / ng) * tiles_per_cta;
-  const int tile_end = min(tile_begin + tiles_per_cta, n_tiles);
-  const int q0 = g * G;
-  const int gq = min(G, B - q0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  if (MODE == kModeMain)
-    for (int i = threadIdx.x; i < gq; i += blockDim.x) s_theta[i] = R > 0 ? __ldg(theta + q0 + i) : 0u;
-  const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
-  const int nterm = n_u[g];
-  const int32_t* ut = u_terms + ebase;
-  const int32_t* up = u_ptr + ebase + g;
-  // fixed-point tail (float impacts, groups whose bound allows it): staged
-  // weights carry the query's scale 2^S_q, rows hold integers until the head
-  // phase (or a conversion pass) turns them into floats
-  const bool fx = IMPACT != GS_IMPACT_U8 && __ldg(fixp + g) != 0;
-  if (fx)
-    for (int i = threadIdx.x; i < gq; i += blockDim.x) {
-      const int S = __ldg(qscale + q0 + i);
-      s_sc[i] = ldexpf(1.0f, S);
-      s_isc[i] = ldexpf(1.0f, -S);
-    }
-  __syncthreads();
-  // the group's (query, weight) entries, staged with the query's row byte offset
-  const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
-  const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
-  const bool staged = (ent_hi - ent_lo) <= kEntCap;
-  const uint32_t row_bytes = (uint32_t)T * 4u;
-  if (staged)
-    for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) {
-      const uint2 E = __ldg(ent + ent_lo + i);
-      ent_s[i] = make_uint2(E.x * row_bytes, fx ? __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]) : E.y);
-    }
-  const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
-  // terms per batch: their 128-posting work items must fit the item table
-  const int items_per_term = T / 128 + 1;
-  const int tb = min(kDtThreads, kItemCap / items_per_term);
-  // a group whose terms fit one batch keeps their ids, first blocks and entry
-  // ranges for all its tiles; only the segment bounds are read per tile
-  const bool one_batch = nterm <= tb;
-  if (one_batch && (int)threadIdx.x < nterm) {
-    const int32_t t = ut[threadIdx.x];
-    s_t[threadIdx.x] = t;
-    s_tb[threadIdx.x] = (int32_t)__ldg(term_block + t);
-    s_e0[threadIdx.x] = __ldg(up + threadIdx.x);
-    if ((int)threadIdx.x == nterm - 1) s_e0[nterm] = __ldg(up + nterm);
+  // Main and sample passes: CTA b scores the run of tiles_per_cta tiles
+  // that starts at tile (b / ng) tiles_per_cta, for query group b % ng; the
+  // group's data are read once and serve all of them.  Recovery passes: a
+  // persistent grid walks the (overflowed group, tile run) units.
+  int n_units = 1, unit0 = 0, ustep = 1, n_ovg = 1;
+  if constexpr (MODE == kModeRecover) {
+    n_ovg = (int)__ldcg(rec.n_groups);
+    n_units = n_ovg * ((n_tiles + tiles_per_cta - 1) / tiles_per_cta);
+    unit0 = blockIdx.x;
+    ustep = gridDim.x;
   }
-  int nact = 0;
-  if (HEAD) {
-    nact = head_nact[g];
-    for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
-    __syncthreads();
-    // FMA head: W[a][q].  Tensor-core head: A fragments of
-    // W[q][a] (q < 16 queries, a < nact rows), k-step ks,
-    // lane (gid, tig): W[gid][8 ks + tig], W[gid + 8][...], W[gid][8 ks + tig + 4],
-    // W[gid + 8][...]; each weight w = high + low, both TF32.  uint8 weights
-    // are integers: exact in TF32 and summed exactly in FP32 while every
-    // partial sum stays below 2^24 (weights <= 1023, 255 per impact, <= 64 rows)
-    if (threadIdx.x == 0) s_tc = HK == kHeadTensor;
-    __syncthreads();
-    if (HK == kHeadFma)
-      for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
-        const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
-        memcpy(&s_w[i], &raw, 4);
-      }
-    const int KS = HK == kHeadTensor ? (nact + 7) / 8 : 0;
-    for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
-      const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
-      uint32_t hi[4], lo[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int q = gid + 8 * (e & 1);
-        const int a = 8 * ks + tig + 4 * (e >> 1);
-        uint32_t raw = 0u;
-        if (a < nact) raw = __ldg(headw + ((int64_t)g * H + s_hact[a]) * kHeadG + q);
-        float w;
-        if (IMPACT == GS_IMPACT_U8) {
-          if ((int32_t)raw > 1023 || (int32_t)raw < 0) s_tc = 0;
-          w = (float)(int32_t)raw;
-        } else {
-          w = __uint_as_float(raw);
-        }
-        hi[e] = to_tf32(w);
-        lo[e] = to_tf32(w - __uint_as_float(hi[e]));
-      }
-      s_af[2 * i] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      s_af[2 * i + 1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
-  }
-
-  for (int tile_idx = tile_begin; tile_idx < tile_end; ++tile_idx) {
-    int tau;
-    if (MODE == kModeSample) {
-      tau = tile_idx * R;
+  for (int unit = unit0; unit < n_units; unit += ustep) {
+    int g, tile_begin;
+    if constexpr (MODE == kModeRecover) {
+      __syncthreads();  // the previous unit's shared state is no longer read
+      g = __ldcg(rec.groups + unit % n_ovg);
+      tile_begin = (unit / n_ovg) * tiles_per_cta;
     } else {
-      tau = tile_idx;
-      if (R > 0 && (tau % R) == 0 && tau / R < n_sample) continue;  // a sample tile: already scored
+      g = blockIdx.x % ng;
+      tile_begin = (blockIdx.x / ng) * tiles_per_cta;
     }
-    const int64_t doc0 = (int64_t)tau * T;
-    const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
-    __syncthreads();  // the previous tile's rows are no longer read
-    {
-      uint4* a4 = reinterpret_cast<uint4*>(acc);
-      for (int i = threadIdx.x; i < G * T / 4; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
-    }
-    // the planning scan's barriers order the clearing before the tail's
-    // reductions; a group without tail terms needs one before the head
-    if (nterm == 0) __syncthreads();
+    const int tile_end = min(tile_begin + tiles_per_cta, n_tiles);
+    const int q0 = g * G;
+    const int gq = min(G, B - q0);
 
-    for (int j0 = 0; j0 < nterm; j0 += tb) {
-      const int j = j0 + threadIdx.x;
-      int items = 0, tiny = 0;
-      if (threadIdx.x < tb && j < nterm) {
-        const int32_t t = one_batch ? s_t[threadIdx.x] : ut[j];
-        const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
-        const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
-        const int64_t tblk = one_batch ? (int64_t)s_tb[threadIdx.x] : __ldg(term_block + t);
-        s_p0[threadIdx.x] = blocks + (tblk + (int64_t)(s >> 5)) * bb;
-        s_off[threadIdx.x] = (int32_t)(s & 31u);
-        s_len[threadIdx.x] = (int32_t)(e - s);
-        if (!one_batch) {
-          s_e0[threadIdx.x] = __ldg(up + j);
-          if ((int)threadIdx.x == tb - 1 || j == nterm - 1) s_e0[threadIdx.x + 1] = __ldg(up + j + 1);
-        }
-        if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
-        else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
+    if (MODE == kModeMain)
+      for (int i = threadIdx.x; i < gq; i += blockDim.x) s_theta[i] = R > 0 ? __ldg(theta + q0 + i) : 0u;
+    if constexpr (MODE == kModeRecover) {
+      // histogram passes: the key prefix resolved so far; emission: theta
+      for (int i = threadIdx.x; i < gq; i += blockDim.x) {
+        s_over[i] = __ldcg(rec.q_over + q0 + i);
+        s_theta[i] = __ldcg((rec.pass < 3 ? rec.prefix : rec.theta) + q0 + i);
       }
-      // one scan of both counts: items (< 2^16 per batch) low, short postings high
-      int tot2;
-      const int x2 = block_excl_scan(items | (tiny << 16), warp_buf, &tot2);
-      const int xi = x2 & 0xffff, xt = x2 >> 16;
-      const int total = tot2 & 0xffff, tiny_total = tot2 >> 16;
-      if (threadIdx.x < tb) {
-        s_item[threadIdx.x] = xi;
-        s_tp[threadIdx.x] = xt;
+    }
+    const int32_t ebase = min(max(q_indptr[q0], 0), q_nnz);
+    const int nterm = n_u[g];
+    const int32_t* ut = u_terms + ebase;
+    const int32_t* up = u_ptr + ebase + g;
+    // fixed-point tail (float impacts, groups whose bound allows it): staged
+    // weights carry the query's scale 2^S_q, rows hold integers until the head
+    // phase (or a conversion pass) turns them into floats
+    // Recovery (float impacts): int64 fixed point with scale 2^(S_q + 30):
+    // |w x| 2^(S_q + 30) <= 2^61 per product and per sum (S_q bounds the tail
+    // score by 2^31), so no sum overflows and each product is rounded to
+    // 2^-(S_q + 31), far inside the tolerance.
+    const bool fx = !REC64 && IMPACT != GS_IMPACT_U8 && __ldg(fixp + g) != 0;
+    const bool scaled = fx || REC64;
+    if (scaled)
+      for (int i = threadIdx.x; i < gq; i += blockDim.x) {
+        const int S = __ldg(qscale + q0 + i) + (REC64 ? 30 : 0);
+        s_sc[i] = ldexpf(1.0f, S);
+        s_isc[i] = ldexpf(1.0f, -S);
       }
-      if (threadIdx.x == 0) s_tp[tb] = tiny_total;
-      for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
-      // packed chunk c starts inside the short segment that holds posting 32 c
-      for (int c = (xt + 31) / 32; 32 * c < xt + tiny; ++c) chunk_j0[c] = (uint16_t)threadIdx.x;
-      const int packed = (tiny_total + 31) / 32;
-      if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    // the group's (query, weight) entries, staged with the query's row byte offset
+    const int32_t ent_lo = nterm > 0 ? __ldg(up) : 0;
+    const int32_t ent_hi = nterm > 0 ? __ldg(up + nterm) : 0;
+    const bool staged = (ent_hi - ent_lo) <= kEntCap;
+    const uint32_t row_bytes = (uint32_t)T * kCell;
+    if (staged)
+      for (int i = threadIdx.x; i < ent_hi - ent_lo; i += blockDim.x) {
+        const uint2 E = __ldg(ent + ent_lo + i);
+        ent_s[i] = make_uint2(E.x * row_bytes, scaled ? __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]) : E.y);
+      }
+    const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+    // terms per batch: their 128-posting work items must fit the item table
+    const int items_per_term = T / 128 + 1;
+    const int tb = min(kDtThreads, kItemCap / items_per_term);
+    // a group whose terms fit one batch keeps their ids, first blocks and entry
+    // ranges for all its tiles; only the segment bounds are read per tile
+    const bool one_batch = nterm <= tb;
+    if (one_batch && (int)threadIdx.x < nterm) {
+      const int32_t t = ut[threadIdx.x];
+      s_t[threadIdx.x] = t;
+      s_tb[threadIdx.x] = (int32_t)__ldg(term_block + t);
+      s_e0[threadIdx.x] = __ldg(up + threadIdx.x);
+      if ((int)threadIdx.x == nterm - 1) s_e0[nterm] = __ldg(up + nterm);
+    }
+    int nact = 0;
+    if (HEAD) {
+      nact = head_nact[g];
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) s_hact[i] = __ldg(head_act + (int64_t)g * H + i);
       __syncthreads();
-      const int units = total + packed;
-      // one (query, weight) entry of the group
-      auto entry = [&](int32_t en) {
-        uint2 E;
-        if (staged) {
-          E = ent_s[en - ent_lo];
-        } else {
-          E = __ldg(ent + en);
-          if (fx) E.y = __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]);
-          E.x *= row_bytes;
+      // FMA head: W[a][q].  Tensor-core head: A fragments of
+      // W[q][a] (q < 16 queries, a < nact rows), k-step ks,
+      // lane (gid, tig): W[gid][8 ks + tig], W[gid + 8][...], W[gid][8 ks + tig + 4],
+      // W[gid + 8][...]; each weight w = high + low, both TF32.  uint8 weights
+      // are integers: exact in TF32 and summed exactly in FP32 while every
+      // partial sum stays below 2^24 (weights <= 1023, 255 per impact, <= 64 rows)
+      if (threadIdx.x == 0) s_tc = HK == kHeadTensor;
+      __syncthreads();
+      if (HK == kHeadFma)
+        for (int i = threadIdx.x; i < nact * kHeadG; i += blockDim.x) {
+          const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
+          memcpy(&s_w[i], &raw, 4);
         }
-        return E;
-      };
-      // one update w x: integer reductions (uint8 impacts, and float impacts
-      // in fixed point, w already scaled by 2^S_q), else float reductions
-      auto red = [&](auto fxc, uint32_t addr, uint32_t wbits, AccT xv) {
-        if constexpr (IMPACT == GS_IMPACT_U8) {
-          asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
-        } else if constexpr (decltype(fxc)::value) {
-          asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr),
-                       "r"(__float2int_rn(__uint_as_float(wbits) * (float)xv))
-                       : "memory");
-        } else {
-          asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
-        }
-      };
-      // item it: lane l loads posting l of each of its 4 blocks; da = byte
-      // offset of the document inside a row, -1 when the lane has no posting
-      auto load_item = [&](int it, int* da, AccT* x) -> int {
-        const int jj = item_term[it];
-        const int c = it - s_item[jj];
-        const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
-        const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
-        const uint32_t len = (uint32_t)s_len[jj];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          da[i] = -1;
-          x[i] = (AccT)0;
-          if ((uint32_t)(rel + 32 * i) < len) {
-            const uint8_t* blk = base + i * bb;
-            const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
-            da[i] = (int)(doc - doc0) * 4;
-            if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
-            else x[i] = (AccT)load_x<IMPACT>(blk, lane);
+      const int KS = HK == kHeadTensor ? (nact + 7) / 8 : 0;
+      for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
+        const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
+        uint32_t hi[4], lo[4];
+  #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = gid + 8 * (e & 1);
+          const int a = 8 * ks + tig + 4 * (e >> 1);
+          uint32_t raw = 0u;
+          if (a < nact) raw = __ldg(headw + ((int64_t)g * H + s_hact[a]) * kHeadG + q);
+          float w;
+          if (IMPACT == GS_IMPACT_U8) {
+            if ((int32_t)raw > 1023 || (int32_t)raw < 0) s_tc = 0;
+            w = (float)(int32_t)raw;
+          } else {
+            w = __uint_as_float(raw);
           }
+          hi[e] = to_tf32(w);
+          lo[e] = to_tf32(w - __uint_as_float(hi[e]));
         }
-        return jj;
-      };
-      // NI loaded items of term jj: every entry of the term, every posting
-      auto score_items = [&](auto fxc, int jj, const int* da, const AccT* x, int ni) {
-        const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
-        for (int32_t en = eb; en < ee; ++en) {
-          const uint2 E = entry(en);
-          const uint32_t row = acc_s + E.x;
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (i < 4 * ni && da[i] >= 0) red(fxc, row + (uint32_t)da[i], E.y, x[i]);
+        s_af[2 * i] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        s_af[2 * i + 1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+
+    for (int tile_idx = tile_begin; tile_idx < tile_end; ++tile_idx) {
+      int tau;
+      if (MODE == kModeSample) {
+        tau = tile_idx * R;
+      } else {
+        tau = tile_idx;
+        // main pass: a sample tile is scored already; recovery: every tile
+        if (MODE == kModeMain && R > 0 && (tau % R) == 0 && tau / R < n_sample) continue;
+      }
+      const int64_t doc0 = (int64_t)tau * T;
+      const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
+      __syncthreads();  // the previous tile's rows are no longer read
+      {
+        uint4* a4 = reinterpret_cast<uint4*>(acc);
+        for (int i = threadIdx.x; i < G * T * kCell / 16; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
+      }
+      // the planning scan's barriers order the clearing before the tail's
+      // reductions; a group without tail terms needs one before the head
+      if (nterm == 0) __syncthreads();
+
+      for (int j0 = 0; j0 < nterm; j0 += tb) {
+        const int j = j0 + threadIdx.x;
+        int items = 0, tiny = 0;
+        if (threadIdx.x < tb && j < nterm) {
+          const int32_t t = one_batch ? s_t[threadIdx.x] : ut[j];
+          const uint32_t* srow = seg + (int64_t)t * (seg_tiles + 1);
+          const uint32_t s = __ldg(srow + seg_lo), e = __ldg(srow + seg_hi);
+          const int64_t tblk = one_batch ? (int64_t)s_tb[threadIdx.x] : __ldg(term_block + t);
+          s_p0[threadIdx.x] = blocks + (tblk + (int64_t)(s >> 5)) * bb;
+          s_off[threadIdx.x] = (int32_t)(s & 31u);
+          s_len[threadIdx.x] = (int32_t)(e - s);
+          if (!one_batch) {
+            s_e0[threadIdx.x] = __ldg(up + j);
+            if ((int)threadIdx.x == tb - 1 || j == nterm - 1) s_e0[threadIdx.x + 1] = __ldg(up + j + 1);
+          }
+          if (e - s >= (uint32_t)kTinySeg) items = (int)((((e - 1) >> 5) - (s >> 5)) / 4 + 1);  // chunks of 4 blocks
+          else tiny = (int)(e - s);  // short segments are packed 32 postings per warp step
         }
-      };
-      // 32 postings of the packed short segments: one posting per lane, its
-      // own term and entries
-      auto score_packed = [&](auto fxc, int it) {
-        const int P = (it - total) * 32 + lane;
-        if (P >= tiny_total) return;
-        int jj = chunk_j0[it - total];
-        while (P >= s_tp[jj + 1]) ++jj;
-        const int rel = P - s_tp[jj] + s_off[jj];
-        const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
-        const int li = rel & 31;
-        const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
-        const uint32_t da = (uint32_t)(doc - doc0) * 4u;
-        AccT xv;
-        if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
-        else xv = (AccT)load_x<IMPACT>(blk, li);
-        const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
-        for (int32_t en = eb; en < ee; ++en) {
-          const uint2 E = entry(en);
-          red(fxc, acc_s + E.x + da, E.y, xv);
+        // one scan of both counts: items (< 2^16 per batch) low, short postings high
+        int tot2;
+        const int x2 = block_excl_scan(items | (tiny << 16), warp_buf, &tot2);
+        const int xi = x2 & 0xffff, xt = x2 >> 16;
+        const int total = tot2 & 0xffff, tiny_total = tot2 >> 16;
+        if (threadIdx.x < tb) {
+          s_item[threadIdx.x] = xi;
+          s_tp[threadIdx.x] = xt;
         }
-      };
-      // units are claimed two at a time; both items' postings are loaded
-      // before either is scored, so that each warp keeps 256 postings in flight
-      auto run_units = [&](auto fxc) {
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&s_next, 2);
-        nxt = __shfl_sync(0xffffffffu, nxt, 0);
-        while (nxt < units) {
-          const int it = nxt;
+        if (threadIdx.x == 0) s_tp[tb] = tiny_total;
+        for (int c = 0; c < items; ++c) item_term[xi + c] = (uint16_t)threadIdx.x;
+        // packed chunk c starts inside the short segment that holds posting 32 c
+        for (int c = (xt + 31) / 32; 32 * c < xt + tiny; ++c) chunk_j0[c] = (uint16_t)threadIdx.x;
+        const int packed = (tiny_total + 31) / 32;
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
+        const int units = total + packed;
+        // one (query, weight) entry of the group
+        auto entry = [&](int32_t en) {
+          uint2 E;
+          if (staged) {
+            E = ent_s[en - ent_lo];
+          } else {
+            E = __ldg(ent + en);
+            if (scaled) E.y = __float_as_uint(__uint_as_float(E.y) * s_sc[E.x]);
+            E.x *= row_bytes;
+          }
+          return E;
+        };
+        // one update w x: integer reductions (uint8 impacts, and float impacts
+        // in fixed point, w already scaled by 2^S_q), else float reductions
+        auto red = [&](auto fxc, uint32_t addr, uint32_t wbits, AccT xv) {
+          if constexpr (REC64) {
+            const long long v = __float2ll_rn(__uint_as_float(wbits) * (float)xv);
+            asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+          } else if constexpr (IMPACT == GS_IMPACT_U8) {
+            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"((int32_t)wbits * (int32_t)xv) : "memory");
+          } else if constexpr (decltype(fxc)::value) {
+            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr),
+                         "r"(__float2int_rn(__uint_as_float(wbits) * (float)xv))
+                         : "memory");
+          } else {
+            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(__uint_as_float(wbits) * (float)xv) : "memory");
+          }
+        };
+        // item it: lane l loads posting l of each of its 4 blocks; da = byte
+        // offset of the document inside a row, -1 when the lane has no posting
+        auto load_item = [&](int it, int* da, AccT* x) -> int {
+          const int jj = item_term[it];
+          const int c = it - s_item[jj];
+          const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
+          const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
+          const uint32_t len = (uint32_t)s_len[jj];
+  #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            da[i] = -1;
+            x[i] = (AccT)0;
+            if ((uint32_t)(rel + 32 * i) < len) {
+              const uint8_t* blk = base + i * bb;
+              const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + lane);
+              da[i] = (int)(doc - doc0) * kCell;
+              if (IMPACT == GS_IMPACT_U8) x[i] = (AccT)__ldg(blk + 128 + lane);
+              else x[i] = (AccT)load_x<IMPACT>(blk, lane);
+            }
+          }
+          return jj;
+        };
+        // NI loaded items of term jj: every entry of the term, every posting
+        auto score_items = [&](auto fxc, int jj, const int* da, const AccT* x, int ni) {
+          const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
+          for (int32_t en = eb; en < ee; ++en) {
+            const uint2 E = entry(en);
+            const uint32_t row = acc_s + E.x;
+  #pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (i < 4 * ni && da[i] >= 0) red(fxc, row + (uint32_t)da[i], E.y, x[i]);
+          }
+        };
+        // 32 postings of the packed short segments: one posting per lane, its
+        // own term and entries
+        auto score_packed = [&](auto fxc, int it) {
+          const int P = (it - total) * 32 + lane;
+          if (P >= tiny_total) return;
+          int jj = chunk_j0[it - total];
+          while (P >= s_tp[jj + 1]) ++jj;
+          const int rel = P - s_tp[jj] + s_off[jj];
+          const uint8_t* blk = s_p0[jj] + (uint32_t)((rel >> 5) * bb);
+          const int li = rel & 31;
+          const int32_t doc = __ldg(reinterpret_cast<const int32_t*>(blk) + li);
+          const uint32_t da = (uint32_t)(doc - doc0) * (uint32_t)kCell;
+          AccT xv;
+          if (IMPACT == GS_IMPACT_U8) xv = (AccT)__ldg(blk + 128 + li);
+          else xv = (AccT)load_x<IMPACT>(blk, li);
+          const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
+          for (int32_t en = eb; en < ee; ++en) {
+            const uint2 E = entry(en);
+            red(fxc, acc_s + E.x + da, E.y, xv);
+          }
+        };
+        // units are claimed two at a time; both items' postings are loaded
+        // before either is scored, so that each warp keeps 256 postings in flight
+        auto run_units = [&](auto fxc) {
+          int nxt = 0;
           if (lane == 0) nxt = atomicAdd(&s_next, 2);
           nxt = __shfl_sync(0xffffffffu, nxt, 0);
-          if (it + 1 < total) {
-            int da[8];
-            AccT x[8];
-            const int ja = load_item(it, da, x);
-            const int jb = load_item(it + 1, da + 4, x + 4);
-            if (ja == jb) {
-              score_items(fxc, ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
-            } else {
-              score_items(fxc, ja, da, x, 1);
-              score_items(fxc, jb, da + 4, x + 4, 1);
-            }
-          } else {
-            for (int u = it; u < min(it + 2, units); ++u) {
-              if (u < total) {
-                int da[4];
-                AccT x[4];
-                const int jj = load_item(u, da, x);
-                score_items(fxc, jj, da, x, 1);
+          while (nxt < units) {
+            const int it = nxt;
+            if (lane == 0) nxt = atomicAdd(&s_next, 2);
+            nxt = __shfl_sync(0xffffffffu, nxt, 0);
+            if (it + 1 < total) {
+              int da[8];
+              AccT x[8];
+              const int ja = load_item(it, da, x);
+              const int jb = load_item(it + 1, da + 4, x + 4);
+              if (ja == jb) {
+                score_items(fxc, ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
               } else {
-                score_packed(fxc, u);
+                score_items(fxc, ja, da, x, 1);
+                score_items(fxc, jb, da + 4, x + 4, 1);
+              }
+            } else {
+              for (int u = it; u < min(it + 2, units); ++u) {
+                if (u < total) {
+                  int da[4];
+                  AccT x[4];
+                  const int jj = load_item(u, da, x);
+                  score_items(fxc, jj, da, x, 1);
+                } else {
+                  score_packed(fxc, u);
+                }
               }
             }
           }
+        };
+        if (fx) run_units(std::true_type{});
+        else run_units(std::false_type{});
+        __syncthreads();
+      }
+      if constexpr (REC64) {
+        // int64 fixed-point sums -> float rows [G][T], in place: float i
+        // takes bytes [4 i, 4 i + 4), inside int64 cell i / 2, so each chunk
+        // of cells is read into registers before any of it is written (the
+        // writes of a chunk reach only cells of this or earlier chunks)
+        constexpr int kPer = 8;
+        const long long* a64 = reinterpret_cast<const long long*>(dyn_smem);
+        float* af = reinterpret_cast<float*>(dyn_smem);
+        const int n_cells = G * T;
+        for (int c0 = 0; c0 < n_cells; c0 += kDtThreads * kPer) {
+          float v[kPer];
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            const int i = c0 + j * kDtThreads + (int)threadIdx.x;
+            v[j] = i < n_cells && i / T < gq ? __ll2float_rn(a64[i]) * s_isc[i / T] : 0.f;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            const int i = c0 + j * kDtThreads + (int)threadIdx.x;
+            if (i < n_cells) af[i] = v[j];
+          }
+          __syncthreads();
         }
-      };
-      if (fx) run_units(std::true_type{});
-      else run_units(std::false_type{});
-      __syncthreads();
-    }
+      }
 
-    if (HEAD) {
-      // dense head: S[q][d] += sum_a W[q][a] X[a][d] over the group's active
-      // head rows a, a contraction of 16 queries x nact rows x T documents.
-      const int ib = impact_bytes(IMPACT);
-      if (HK == kHeadFma) {
-        // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
-        // documents 2 p, 2 p + 1 of each slab of kSlab documents,
-        // p = 32 w + l: the head rows are read coalesced, four rows in
-        // flight, the weights are warp-wide broadcasts, and every (query,
-        // document) cell has one owner (no atomics)
-        constexpr int kSlab = 2 * kDtThreads;
-        const int dp = warp * 32 + lane;
-        for (int slab = 0; slab < T; slab += kSlab) {
-          if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
-          const int64_t col = doc0 + slab + 2 * dp;
-          AccT r[16][2];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
-          auto load2 = [&](int a, AccT& x0, AccT& x1) {
-            const int64_t at = (int64_t)s_hact[a] * head_ld + col;
-            if (IMPACT == GS_IMPACT_F32) {
-              const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
-              x0 = u.x;
-              x1 = u.y;
-            } else if (IMPACT == GS_IMPACT_U8) {
-              const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
-              x0 = (AccT)(u & 0xffu);
-              x1 = (AccT)(u >> 8);
-            } else {
-              const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
-              float2 f;
-              if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
-              else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
-              x0 = (AccT)f.x;
-              x1 = (AccT)f.y;
-            }
-          };
-          for (int a0 = 0; a0 < nact; a0 += 4) {
-            AccT xs[4][2];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              xs[u][0] = xs[u][1] = (AccT)0;
-              if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (a0 + u >= nact) break;
-              const AccT* wr = s_w + (a0 + u) * kHeadG;
-#pragma unroll
-              for (int q4 = 0; q4 < 4; ++q4) {
-                AccT w4[4];
-                *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                  if (IMPACT == GS_IMPACT_U8) {
-                    r[4 * q4 + v][0] += w4[v] * xs[u][0];
-                    r[4 * q4 + v][1] += w4[v] * xs[u][1];
-                  } else {
-                    r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
-                    r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+      if (HEAD) {
+        // dense head: S[q][d] += sum_a W[q][a] X[a][d] over the group's active
+        // head rows a, a contraction of 16 queries x nact rows x T documents.
+        const int ib = impact_bytes(IMPACT);
+        if (HK == kHeadFma) {
+          // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
+          // documents 2 p, 2 p + 1 of each slab of kSlab documents,
+          // p = 32 w + l: the head rows are read coalesced, four rows in
+          // flight, the weights are warp-wide broadcasts, and every (query,
+          // document) cell has one owner (no atomics)
+          constexpr int kSlab = 2 * kDtThreads;
+          const int dp = warp * 32 + lane;
+          for (int slab = 0; slab < T; slab += kSlab) {
+            if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
+            const int64_t col = doc0 + slab + 2 * dp;
+            AccT r[16][2];
+  #pragma unroll
+            for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
+            auto load2 = [&](int a, AccT& x0, AccT& x1) {
+              const int64_t at = (int64_t)s_hact[a] * head_ld + col;
+              if (IMPACT == GS_IMPACT_F32) {
+                const float2 u = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(head_dense) + at));
+                x0 = u.x;
+                x1 = u.y;
+              } else if (IMPACT == GS_IMPACT_U8) {
+                const uint16_t u = __ldg(reinterpret_cast<const uint16_t*>(head_dense + at));
+                x0 = (AccT)(u & 0xffu);
+                x1 = (AccT)(u >> 8);
+              } else {
+                const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(head_dense + at * 2));
+                float2 f;
+                if (IMPACT == GS_IMPACT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+                else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+                x0 = (AccT)f.x;
+                x1 = (AccT)f.y;
+              }
+            };
+            for (int a0 = 0; a0 < nact; a0 += 4) {
+              AccT xs[4][2];
+  #pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                xs[u][0] = xs[u][1] = (AccT)0;
+                if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+              }
+  #pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (a0 + u >= nact) break;
+                const AccT* wr = s_w + (a0 + u) * kHeadG;
+  #pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                  AccT w4[4];
+                  *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
+  #pragma unroll
+                  for (int v = 0; v < 4; ++v) {
+                    if (IMPACT == GS_IMPACT_U8) {
+                      r[4 * q4 + v][0] += w4[v] * xs[u][0];
+                      r[4 * q4 + v][1] += w4[v] * xs[u][1];
+                    } else {
+                      r[4 * q4 + v][0] = fmaf((float)w4[v], (float)xs[u][0], (float)r[4 * q4 + v][0]);
+                      r[4 * q4 + v][1] = fmaf((float)w4[v], (float)xs[u][1], (float)r[4 * q4 + v][1]);
+                    }
                   }
                 }
               }
             }
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int q = i;
-            if (q < gq) {
-              AccT* dst = acc + q * T + slab + 2 * dp;
-              uint2 c = *reinterpret_cast<uint2*>(dst);
-              AccT* v = reinterpret_cast<AccT*>(&c);
-              if constexpr (IMPACT == GS_IMPACT_U8) {
-                v[0] += r[i][0];
-                v[1] += r[i][1];
-              } else {
-                v[0] = tail_value(v[0], fx, s_isc[q]) + r[i][0];
-                v[1] = tail_value(v[1], fx, s_isc[q]) + r[i][1];
+  #pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int q = i;
+              if (q < gq) {
+                AccT* dst = acc + q * T + slab + 2 * dp;
+                uint2 c = *reinterpret_cast<uint2*>(dst);
+                AccT* v = reinterpret_cast<AccT*>(&c);
+                if constexpr (IMPACT == GS_IMPACT_U8) {
+                  v[0] += r[i][0];
+                  v[1] += r[i][1];
+                } else {
+                  v[0] = tail_value(v[0], fx, s_isc[q]) + r[i][0];
+                  v[1] = tail_value(v[1], fx, s_isc[q]) + r[i][1];
+                }
+                *reinterpret_cast<uint2*>(dst) = c;
               }
-              *reinterpret_cast<uint2*>(dst) = c;
             }
           }
-        }
-      } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
-        // tensor cores: m16n8k8 TF32 MMAs, M = the 16 queries, K = 8 rows,
-        // N = 8 documents.  A warp step covers 8 NT documents base + 0.. as
-        // NT MMA tiles: column n of tile j is document base + NT n + j, so
-        // that lane (gid, tig) reads documents base + NT gid .. + NT - 1 of a
-        // row with one vector load (its B operand for all NT tiles) and owns
-        // documents base + 2 NT tig .. + 2 NT - 1 of queries gid, gid + 8 in
-        // the D fragments.  Every (query, document) cell has one owner (no
-        // atomics).  W = high + low TF32 parts, and X too for FP32 impacts
-        // (FP16, BF16 and uint8 impacts are exact in TF32), keeps FP32
-        // accuracy; uint8 weights are exact integers: high part only.
-        constexpr int NT = 4;
-        constexpr int KB = IMPACT == GS_IMPACT_F32 ? 2 : 4;  // k-steps whose operands are loaded together
-        using VecT = typename std::conditional<
-            IMPACT == GS_IMPACT_U8, uint32_t,
-            typename std::conditional<IMPACT == GS_IMPACT_F32, float4, uint2>::type>::type;
-        const int gid = lane >> 2, tig = lane & 3;
-        const int KS = (nact + 7) / 8;
-        for (int cb = warp * 8 * NT; cb < T; cb += kDtThreads / 32 * 8 * NT) {
-          const int64_t col = doc0 + cb + NT * gid;
-          float d[NT][4];
-#pragma unroll
-          for (int j = 0; j < NT; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
-          for (int k0 = 0; k0 < KS; k0 += KB) {
-            VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, NT documents each
-#pragma unroll
-            for (int u = 0; u < KB; ++u)
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int r = 8 * (k0 + u) + tig + 4 * h;
-                xv[u][h] = VecT{};
-                if (r < nact)
-                  xv[u][h] = __ldg(reinterpret_cast<const VecT*>(head_dense + ((int64_t)s_hact[r] * head_ld + col) * ib));
+        } else if (IMPACT != GS_IMPACT_U8 || s_tc) {
+          // tensor cores: m16n8k8 TF32 MMAs, M = the 16 queries, K = 8 rows,
+          // N = 8 documents.  A warp step covers 8 NT documents base + 0.. as
+          // NT MMA tiles: column n of tile j is document base + NT n + j, so
+          // that lane (gid, tig) reads documents base + NT gid .. + NT - 1 of a
+          // row with one vector load (its B operand for all NT tiles) and owns
+          // documents base + 2 NT tig .. + 2 NT - 1 of queries gid, gid + 8 in
+          // the D fragments.  Every (query, document) cell has one owner (no
+          // atomics).  W = high + low TF32 parts, and X too for FP32 impacts
+          // (FP16, BF16 and uint8 impacts are exact in TF32), keeps FP32
+          // accuracy; uint8 weights are exact integers: high part only.
+          constexpr int NT = 4;
+          constexpr int KB = IMPACT == GS_IMPACT_F32 ? 2 : 4;  // k-steps whose operands are loaded together
+          using VecT = typename std::conditional<
+              IMPACT == GS_IMPACT_U8, uint32_t,
+              typename std::conditional<IMPACT == GS_IMPACT_F32, float4, uint2>::type>::type;
+          const int gid = lane >> 2, tig = lane & 3;
+          const int KS = (nact + 7) / 8;
+          for (int cb = warp * 8 * NT; cb < T; cb += kDtThreads / 32 * 8 * NT) {
+            const int64_t col = doc0 + cb + NT * gid;
+            float d[NT][4];
+  #pragma unroll
+            for (int j = 0; j < NT; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
+            for (int k0 = 0; k0 < KS; k0 += KB) {
+              VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, NT documents each
+  #pragma unroll
+              for (int u = 0; u < KB; ++u)
+  #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int r = 8 * (k0 + u) + tig + 4 * h;
+                  xv[u][h] = VecT{};
+                  if (r < nact)
+                    xv[u][h] = __ldg(reinterpret_cast<const VecT*>(head_dense + ((int64_t)s_hact[r] * head_ld + col) * ib));
+                }
+  #pragma unroll
+              for (int u = 0; u < KB; ++u) {
+                if (k0 + u >= KS) break;
+                const uint4 ah = s_af[2 * ((k0 + u) * 32 + lane)];
+                const uint32_t a_hi[4] = {ah.x, ah.y, ah.z, ah.w};
+                uint32_t a_lo[4] = {0u, 0u, 0u, 0u};
+                if (IMPACT != GS_IMPACT_U8) {
+                  const uint4 al = s_af[2 * ((k0 + u) * 32 + lane) + 1];
+                  a_lo[0] = al.x; a_lo[1] = al.y; a_lo[2] = al.z; a_lo[3] = al.w;
+                }
+  #pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                  if constexpr (IMPACT == GS_IMPACT_F32) {
+                    // x = high + low TF32 parts as well: three products
+                    const float x0 = f4_get(xv[u][0], j), x1 = f4_get(xv[u][1], j);
+                    const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
+                    const uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
+                    mma_tf32(d[j], a_lo, h0, h1);
+                    mma_tf32(d[j], a_hi, l0, l1);
+                    mma_tf32(d[j], a_hi, h0, h1);
+                  } else {
+                    const uint32_t b0 = impact_tf32<IMPACT>(xv[u][0], j), b1 = impact_tf32<IMPACT>(xv[u][1], j);
+                    if (IMPACT != GS_IMPACT_U8) mma_tf32(d[j], a_lo, b0, b1);
+                    mma_tf32(d[j], a_hi, b0, b1);
+                  }
+                }
               }
-#pragma unroll
-            for (int u = 0; u < KB; ++u) {
-              if (k0 + u >= KS) break;
-              const uint4 ah = s_af[2 * ((k0 + u) * 32 + lane)];
-              const uint32_t a_hi[4] = {ah.x, ah.y, ah.z, ah.w};
-              uint32_t a_lo[4] = {0u, 0u, 0u, 0u};
-              if (IMPACT != GS_IMPACT_U8) {
-                const uint4 al = s_af[2 * ((k0 + u) * 32 + lane) + 1];
-                a_lo[0] = al.x; a_lo[1] = al.y; a_lo[2] = al.z; a_lo[3] = al.w;
-              }
-#pragma unroll
-              for (int j = 0; j < NT; ++j) {
-                if constexpr (IMPACT == GS_IMPACT_F32) {
-                  // x = high + low TF32 parts as well: three products
-                  const float x0 = f4_get(xv[u][0], j), x1 = f4_get(xv[u][1], j);
-                  const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
-                  const uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
-                  mma_tf32(d[j], a_lo, h0, h1);
-                  mma_tf32(d[j], a_hi, l0, l1);
-                  mma_tf32(d[j], a_hi, h0, h1);
+            }
+            // D: (query gid + 8 h, document cb + 2 NT tig + NT c + j) = d[j][2 h + c]
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int q = gid + 8 * h;
+              if (q >= gq) continue;
+  #pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                AccT* dst = acc + q * T + cb + 2 * NT * tig + NT * c;
+                if constexpr (IMPACT == GS_IMPACT_U8) {
+                  int4 v = *reinterpret_cast<int4*>(dst);
+                  v.x += __float2int_rn(d[0][2 * h + c]);
+                  v.y += __float2int_rn(d[1][2 * h + c]);
+                  v.z += __float2int_rn(d[2][2 * h + c]);
+                  v.w += __float2int_rn(d[3][2 * h + c]);
+                  *reinterpret_cast<int4*>(dst) = v;
                 } else {
-                  const uint32_t b0 = impact_tf32<IMPACT>(xv[u][0], j), b1 = impact_tf32<IMPACT>(xv[u][1], j);
-                  if (IMPACT != GS_IMPACT_U8) mma_tf32(d[j], a_lo, b0, b1);
-                  mma_tf32(d[j], a_hi, b0, b1);
+                  float4 v = *reinterpret_cast<float4*>(dst);
+                  const float isc = s_isc[q];
+                  v.x = tail_value(v.x, fx, isc) + d[0][2 * h + c];
+                  v.y = tail_value(v.y, fx, isc) + d[1][2 * h + c];
+                  v.z = tail_value(v.z, fx, isc) + d[2][2 * h + c];
+                  v.w = tail_value(v.w, fx, isc) + d[3][2 * h + c];
+                  *reinterpret_cast<float4*>(dst) = v;
                 }
               }
             }
           }
-          // D: (query gid + 8 h, document cb + 2 NT tig + NT c + j) = d[j][2 h + c]
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int q = gid + 8 * h;
-            if (q >= gq) continue;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              AccT* dst = acc + q * T + cb + 2 * NT * tig + NT * c;
-              if constexpr (IMPACT == GS_IMPACT_U8) {
-                int4 v = *reinterpret_cast<int4*>(dst);
-                v.x += __float2int_rn(d[0][2 * h + c]);
-                v.y += __float2int_rn(d[1][2 * h + c]);
-                v.z += __float2int_rn(d[2][2 * h + c]);
-                v.w += __float2int_rn(d[3][2 * h + c]);
-                *reinterpret_cast<int4*>(dst) = v;
-              } else {
-                float4 v = *reinterpret_cast<float4*>(dst);
-                const float isc = s_isc[q];
-                v.x = tail_value(v.x, fx, isc) + d[0][2 * h + c];
-                v.y = tail_value(v.y, fx, isc) + d[1][2 * h + c];
-                v.z = tail_value(v.z, fx, isc) + d[2][2 * h + c];
-                v.w = tail_value(v.w, fx, isc) + d[3][2 * h + c];
-                *reinterpret_cast<float4*>(dst) = v;
+        } else {
+          // uint8 weights too large for exact FP32 sums: integer FMAs, thread
+          // (warp w, lane l) owns the 16 queries and documents 2 p, 2 p + 1 of
+          // each 1024-document slab, p = 32 w + l
+          for (int slab = 0; slab < T; slab += 2 * kDtThreads) {
+            const int dp = warp * 32 + lane;
+            if (slab + 2 * dp >= T) break;
+            const int64_t col = doc0 + slab + 2 * dp;
+            int32_t r[16][2];
+  #pragma unroll
+            for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0;
+            for (int a = 0; a < nact; ++a) {
+              const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(head_dense + (int64_t)s_hact[a] * head_ld + col));
+              const int32_t x0 = v & 0xff, x1 = v >> 8;
+              const uint32_t* wr = headw + ((int64_t)g * H + s_hact[a]) * kHeadG;
+  #pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int32_t w = (int32_t)__ldg(wr + i);
+                r[i][0] += w * x0;
+                r[i][1] += w * x1;
+              }
+            }
+  #pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (i < gq) {
+                int2* dst = reinterpret_cast<int2*>(acc + i * T + slab + 2 * dp);
+                int2 c = *dst;
+                c.x += r[i][0];
+                c.y += r[i][1];
+                *dst = c;
               }
             }
           }
         }
-      } else {
-        // uint8 weights too large for exact FP32 sums: integer FMAs, thread
-        // (warp w, lane l) owns the 16 queries and documents 2 p, 2 p + 1 of
-        // each 1024-document slab, p = 32 w + l
-        for (int slab = 0; slab < T; slab += 2 * kDtThreads) {
-          const int dp = warp * 32 + lane;
-          if (slab + 2 * dp >= T) break;
-          const int64_t col = doc0 + slab + 2 * dp;
-          int32_t r[16][2];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0;
-          for (int a = 0; a < nact; ++a) {
-            const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(head_dense + (int64_t)s_hact[a] * head_ld + col));
-            const int32_t x0 = v & 0xff, x1 = v >> 8;
-            const uint32_t* wr = headw + ((int64_t)g * H + s_hact[a]) * kHeadG;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int32_t w = (int32_t)__ldg(wr + i);
-              r[i][0] += w * x0;
-              r[i][1] += w * x1;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (i < gq) {
-              int2* dst = reinterpret_cast<int2*>(acc + i * T + slab + 2 * dp);
-              int2 c = *dst;
-              c.x += r[i][0];
-              c.y += r[i][1];
-              *dst = c;
-            }
-          }
-        }
+        __syncthreads();
+      } else if (fx) {
+        // no head: fixed-point rows become floats
+        float* af = reinterpret_cast<float*>(acc);
+        for (int i = threadIdx.x; i < gq * T; i += blockDim.x) af[i] = tail_value(af[i], true, s_isc[i / T]);
+        __syncthreads();
       }
-      __syncthreads();
-    } else if (fx) {
-      // no head: fixed-point rows become floats
-      float* af = reinterpret_cast<float*>(acc);
-      for (int i = threadIdx.x; i < gq * T; i += blockDim.x) af[i] = tail_value(af[i], true, s_isc[i / T]);
-      __syncthreads();
-    }
 
-    // epilogue: each warp step covers 128 documents of one query row (4 per lane)
-    const int cpr = T / 128;  // chunks per row
-    if (MODE == kModeSample) {
-      for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
-        const int ql = ci / cpr;
-        const int d0 = (ci - ql * cpr) * 128 + lane * 4;
-        *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
-            *reinterpret_cast<const uint4*>(acc + ql * T + d0);
+      // epilogue: each warp step covers 128 documents of one query row (4 per lane)
+      const int cpr = T / 128;  // chunks per row
+      if (MODE == kModeSample) {
+        for (int ci = warp; ci < gq * cpr; ci += kDtThreads / 32) {
+          const int ql = ci / cpr;
+          const int d0 = (ci - ql * cpr) * 128 + lane * 4;
+          *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
+              *reinterpret_cast<const uint4*>(acc + ql * T + d0);
+        }
+        continue;
       }
-      continue;
-    }
-    // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
-    // whole query rows and walks them in windows of 1024 documents: lane l
-    // compares documents 128 c + 4 l .. + 3 of chunk c = 0..7 and keeps one bit
-    // per document in two masks (above theta_q, equal to theta_q); one warp
-    // scan and one global atomic per window reserve the candidate slots, and
-    // each lane writes its own candidates.  No block barrier.
-    const int64_t n_in = N - doc0;  // documents of this tile inside the collection
-    for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
-      const int q = q0 + ql;
-      const uint32_t th = s_theta[ql];
-      const AccT* row = acc + ql * T;
-      for (int w0 = 0; w0 < T; w0 += 1024) {
-        // one compare per document (score >= theta_q); the few hits are then
-        // split into candidates (> theta_q) and ties (== theta_q)
-        uint32_t ge_bits = 0;
-        const int nc = min(8, (T - w0) / 128);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c >= nc) break;
-          const int d0 = w0 + c * 128 + lane * 4;
-          const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
-          const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            bool ge;
-            if (IMPACT == GS_IMPACT_U8) ge = (int32_t)rv[i] >= (int32_t)th;
-            else ge = __uint_as_float(rv[i]) >= __uint_as_float(th);
-            ge_bits |= (uint32_t)(ge || R <= 0) << (4 * c + i);
+      const int64_t n_in = N - doc0;  // documents of this tile inside the collection
+      if constexpr (MODE == kModeRecover) {
+        if (rec.pass < 3) {
+          // radix-select pass: histogram of key digit `pass` (11, 11, 10 bits
+          // from the top) over the documents whose higher digits match the
+          // prefix resolved so far, warp-aggregated global atomics
+          const int shift = rec.pass == 0 ? 21 : (rec.pass == 1 ? 10 : 0);
+          const uint32_t pmask = rec.pass == 0 ? 0u : (rec.pass == 1 ? 0xFFE00000u : 0xFFFFFC00u);
+          const uint32_t dmask = rec.pass == 2 ? 1023u : 2047u;
+          for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
+            if (!s_over[ql]) continue;
+            const uint32_t pre = s_theta[ql] & pmask;  // pass 0: no digit resolved yet
+            const AccT* row = acc + ql * T;
+            uint32_t* h = rec.hist + (int64_t)(q0 + ql) * 2048;
+            for (int d0 = 0; d0 < T; d0 += 32) {
+              const int d = d0 + lane;
+              int bin = -1;
+              if ((int64_t)d < n_in) {
+                const uint32_t key = score_key(row[d]);
+                if ((key & pmask) == pre) bin = (int)((key >> shift) & dmask);
+              }
+              const unsigned peers = __match_any_sync(0xffffffffu, bin);
+              if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(h + bin, (uint32_t)__popc(peers));
+            }
           }
+          continue;
         }
-        if (n_in < (int64_t)(w0 + 1024)) {
-          // the collection ends inside this window: drop documents >= N
-          uint32_t keep = 0;
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
-          ge_bits &= keep;
-        }
-        uint32_t gt_bits = ge_bits, eq_bits = 0;
-        if (R > 0) {
-          gt_bits = 0;
-          for (uint32_t rem = ge_bits; rem; rem &= rem - 1) {
-            const int bit = __ffs(rem) - 1;
-            const AccT v = row[w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3)];
-            bool gt;
-            if (IMPACT == GS_IMPACT_U8) gt = (int32_t)v > (int32_t)th;
-            else gt = v > __uint_as_float(th);
-            if (gt) gt_bits |= 1u << bit;
-            else eq_bits |= 1u << bit;
+      }
+      // candidates above theta_q and the tie bitmap at theta_q.  Each warp owns
+      // whole query rows and walks them in windows of 1024 documents: lane l
+      // compares documents 128 c + 4 l .. + 3 of chunk c = 0..7 and keeps one bit
+      // per document in two masks (above theta_q, equal to theta_q); one warp
+      // scan and one global atomic per window reserve the candidate slots, and
+      // each lane writes its own candidates.  No block barrier.
+      for (int ql = warp; ql < gq; ql += kDtThreads / 32) {
+        if (MODE == kModeRecover && !s_over[ql]) continue;  // its top-k is final already
+        const int q = q0 + ql;
+        const uint32_t th = s_theta[ql];
+        const AccT* row = acc + ql * T;
+        for (int w0 = 0; w0 < T; w0 += 1024) {
+          // one compare per document (score >= theta_q); the few hits are then
+          // split into candidates (> theta_q) and ties (== theta_q)
+          uint32_t ge_bits = 0;
+          const int nc = min(8, (T - w0) / 128);
+  #pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c >= nc) break;
+            const int d0 = w0 + c * 128 + lane * 4;
+            const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
+            const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+  #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              bool ge;
+              if (IMPACT == GS_IMPACT_U8) ge = (int32_t)rv[i] >= (int32_t)th;
+              else ge = __uint_as_float(rv[i]) >= __uint_as_float(th);
+              ge_bits |= (uint32_t)(ge || R <= 0) << (4 * c + i);
+            }
           }
-        }
-        const int n_gt = __popc(gt_bits);
-        int incl = n_gt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        if (tot > 0) {
-          uint32_t base = 0;
-          if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
-          base = __shfl_sync(0xffffffffu, base, 0);
-          uint32_t slot = base + (uint32_t)(incl - n_gt);
-          while (gt_bits) {
-            const int bit = __ffs(gt_bits) - 1;
-            gt_bits &= gt_bits - 1;
-            const int d = w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3);
-            if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(row[d]), (uint32_t)(doc0 + d));
-            ++slot;
+          if (n_in < (int64_t)(w0 + 1024)) {
+            // the collection ends inside this window: drop documents >= N
+            uint32_t keep = 0;
+  #pragma unroll
+            for (int c = 0; c < 8; ++c)
+  #pragma unroll
+              for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
+            ge_bits &= keep;
           }
-        }
-        if (__any_sync(0xffffffffu, eq_bits != 0)) {
-          // tie words: 32 documents = 8 lanes x 4 bits of one chunk
-          for (int c = 0; c < nc; ++c) {
-            uint32_t word = ((eq_bits >> (4 * c)) & 15u) << (4 * (lane & 7));
-            word |= __shfl_xor_sync(0xffffffffu, word, 1);
-            word |= __shfl_xor_sync(0xffffffffu, word, 2);
-            word |= __shfl_xor_sync(0xffffffffu, word, 4);
-            const int64_t wdoc = doc0 + w0 + c * 128 + (lane >> 3) * 32;
-            if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+          uint32_t gt_bits = ge_bits, eq_bits = 0;
+          if (R > 0) {
+            gt_bits = 0;
+            for (uint32_t rem = ge_bits; rem; rem &= rem - 1) {
+              const int bit = __ffs(rem) - 1;
+              const AccT v = row[w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3)];
+              bool gt;
+              if (IMPACT == GS_IMPACT_U8) gt = (int32_t)v > (int32_t)th;
+              else gt = v > __uint_as_float(th);
+              if (gt) gt_bits |= 1u << bit;
+              else eq_bits |= 1u << bit;
+            }
+          }
+          const int n_gt = __popc(gt_bits);
+          int incl = n_gt;
+  #pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int tot = __shfl_sync(0xffffffffu, incl, 31);
+          if (tot > 0) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            uint32_t slot = base + (uint32_t)(incl - n_gt);
+            while (gt_bits) {
+              const int bit = __ffs(gt_bits) - 1;
+              gt_bits &= gt_bits - 1;
+              const int d = w0 + (bit >> 2) * 128 + lane * 4 + (bit & 3);
+              if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(score_key(row[d]), (uint32_t)(doc0 + d));
+              ++slot;
+            }
+          }
+          if (__any_sync(0xffffffffu, eq_bits != 0)) {
+            // tie words: 32 documents = 8 lanes x 4 bits of one chunk
+            for (int c = 0; c < nc; ++c) {
+              uint32_t word = ((eq_bits >> (4 * c)) & 15u) << (4 * (lane & 7));
+              word |= __shfl_xor_sync(0xffffffffu, word, 1);
+              word |= __shfl_xor_sync(0xffffffffu, word, 2);
+              word |= __shfl_xor_sync(0xffffffffu, word, 4);
+              const int64_t wdoc = doc0 + w0 + c * 128 + (lane >> 3) * 32;
+              if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
+            }
           }
         }
       }
@@ -1007,14 +1133,31 @@ __global__ void dt_sample_emit_kernel(const uint32_t* __restrict__ samp, int64_t
   }
 }
 
+// Recovery bookkeeping written by the first final pass (device workspace).
+struct DtOverflow {
+  uint32_t* q_over;   // [B]
+  uint32_t* g_mark;   // [ng]
+  uint32_t* n_groups;
+  int32_t* groups;    // [ng]
+  uint32_t* hist;     // [B][2048]
+  uint32_t* tiebm;    // [B][bm_words]
+  int G;
+};
+
 // Final exact top-k of each query from its candidates (and ties).
-template <typename ST>
+// First pass (REC = false): a query whose candidate list overflowed (more
+// documents beat theta_q than the list holds) gets no result here; it is
+// marked, its group joins the recovery list, and its histogram row, tie row
+// and candidate count are cleared for the recovery passes.  Recovery pass
+// (REC = true): only the marked queries, whose candidates now lie above
+// their exact k-th score (fewer than k of them) and whose ties sit at it.
+template <typename ST, bool REC>
 __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict__ cand,
-                                                        const uint32_t* __restrict__ cand_cnt, int64_t cap,
+                                                        uint32_t* __restrict__ cand_cnt, int64_t cap,
                                                         const uint32_t* __restrict__ tiebm, int64_t bm_words,
                                                         int64_t N, const uint32_t* __restrict__ theta_bits, int R,
                                                         int k, int32_t* __restrict__ out_ids,
-                                                        ST* __restrict__ out_scores, uint32_t* flags) {
+                                                        ST* __restrict__ out_scores, uint32_t* flags, DtOverflow ov) {
   __shared__ uint32_t hist[2048];
   __shared__ uint32_t ck[GS_MAX_K];
   __shared__ int32_t cid[GS_MAX_K];
@@ -1023,8 +1166,20 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   __shared__ int s_need;
   __shared__ int s_fill;
   const int q = blockIdx.x;
-  const uint32_t raw = cand_cnt[q];
-  if (raw > cap && threadIdx.x == 0) atomicOr(flags, kFlagCandOverflow);
+  if (REC && __ldcg(ov.q_over + q) == 0u) return;
+  const uint32_t raw = __ldcg(cand_cnt + q);
+  if (!REC && raw > cap) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, kFlagCandOverflow);
+      ov.q_over[q] = 1u;
+      cand_cnt[q] = 0u;
+      const int g = q / ov.G;
+      if (atomicExch(ov.g_mark + g, 1u) == 0u) ov.groups[atomicAdd(ov.n_groups, 1u)] = g;
+    }
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) ov.hist[(int64_t)q * 2048 + i] = 0u;
+    for (int64_t w = threadIdx.x; w < bm_words; w += blockDim.x) ov.tiebm[(int64_t)q * bm_words + w] = 0u;
+    return;
+  }
   const int64_t n = min((int64_t)raw, cap);
   const uint2* c = cand + (int64_t)q * cap;
   if (threadIdx.x == 0) s_fill = 0;
@@ -1076,27 +1231,102 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
   }
 }
 
+// One radix-select step of the recovery, one CTA per marked query: from the
+// histogram of key digit `pass` over the documents that match the prefix
+// resolved so far, the digit of the k-th largest key and how many documents
+// with the extended prefix still belong to the top k.  The histogram row is
+// cleared for the next pass.  After the last digit the prefix is the exact
+// k-th largest key, stored as a score (raw bits) in theta.
+template <typename ST>
+__global__ void __launch_bounds__(1024) dt_over_select_kernel(const uint32_t* __restrict__ q_over,
+                                                              uint32_t* __restrict__ hist,
+                                                              uint32_t* __restrict__ prefix, int32_t* __restrict__ need,
+                                                              uint32_t* __restrict__ theta, int pass, int k) {
+  __shared__ uint32_t h[2048];
+  __shared__ int warp_buf[32];
+  __shared__ uint32_t s_digit;
+  __shared__ int s_need;
+  const int q = blockIdx.x;
+  if (__ldcg(q_over + q) == 0u) return;
+  const int nb = pass == 2 ? 1024 : 2048;
+  const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+  uint32_t* hr = hist + (int64_t)q * 2048;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    h[i] = __ldcg(hr + i);
+    hr[i] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    s_digit = 0u;
+    s_need = 1;
+  }
+  __syncthreads();
+  const int need_in = pass == 0 ? k : __ldcg(need + q);
+  // thread j sums bins nb - 1 - (j per + u), u < per, counted from the top
+  const int per = nb / (int)blockDim.x;
+  int local = 0;
+  for (int u = 0; u < per; ++u) local += (int)h[nb - 1 - ((int)threadIdx.x * per + u)];
+  int tot;
+  int above = block_excl_scan(local, warp_buf, &tot);
+  for (int u = 0; u < per; ++u) {
+    const int b = nb - 1 - ((int)threadIdx.x * per + u);
+    const int c = (int)h[b];
+    if (above < need_in && need_in <= above + c) {
+      s_digit = (uint32_t)b;
+      s_need = need_in - above;
+    }
+    above += c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t pf = (pass == 0 ? 0u : __ldcg(prefix + q)) | (s_digit << shift);
+    prefix[q] = pf;
+    need[q] = s_need;
+    if (pass == 2) {
+      const ST v = key_to_score<ST>(pf);
+      uint32_t bits;
+      memcpy(&bits, &v, 4);
+      theta[q] = bits;
+    }
+  }
+}
+
 constexpr size_t kDynSmemFixed = kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
 
 // Raises the dynamic shared-memory ceiling of both tile kernels of this
 // form, once per device: no attribute call is issued while a stream is
 // being captured for a graph.
+// Recovery passes keep 8-byte tail accumulators for float impacts.
+constexpr size_t rec_acc_bytes(int impact) { return impact == GS_IMPACT_U8 ? kDtMaxAccBytes : 2 * kDtMaxAccBytes; }
+
+// Raises the dynamic shared-memory ceiling of the tile kernels of this form
+// and records the recovery kernel's resident CTAs per SM (at its largest
+// tile), once per device: no attribute call is issued while a stream is
+// being captured for a graph.
 template <int IMPACT, int HK>
-gs_status tile_smem_attr() {
+gs_status tile_smem_attr(int* rec_per_sm = nullptr) {
   static std::mutex mu;
   static bool done[128] = {};
+  static int rec_ctas[128] = {};
   int dev = 0;
   GS_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev < 0 || dev >= 128) return GS_ERR_UNSUPPORTED;
   if (!done[dev]) {
     const int ceil_bytes = (int)(kDtMaxAccBytes + kDynSmemFixed);
+    const int rec_bytes = (int)(rec_acc_bytes(IMPACT) + kDynSmemFixed);
     GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeSample, HK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
     GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeMain, HK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, ceil_bytes));
+    GS_CUDA_TRY(cudaFuncSetAttribute(dt_tile_kernel<IMPACT, kModeRecover, HK>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, rec_bytes));
+    int n = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dt_tile_kernel<IMPACT, kModeRecover, HK>,
+                                                              kDtThreads, rec_bytes));
+    rec_ctas[dev] = std::max(n, 1);
     done[dev] = true;
   }
+  if (rec_per_sm) *rec_per_sm = rec_ctas[dev];
   return GS_OK;
 }
 
@@ -1130,7 +1360,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
         ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
         c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
         p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, ms, c.n_sample,
-        p.fixp, p.qscale);
+        p.fixp, p.qscale, DtRecover{});
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
@@ -1149,15 +1379,56 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
       ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
       c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
       p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, mm, c.nt,
-      p.fixp, p.qscale);
+      p.fixp, p.qscale, DtRecover{});
   GS_LAUNCH_CHECK();
   record_stage(opts, 4, s);
   return GS_OK;
 }
 
+// Exact recovery of the queries whose candidate list overflowed (marked by
+// the first final pass): a radix select of their exact k-th largest score
+// over freshly computed scores of every document (three histogram passes of
+// 11, 11 and 10 key bits, each followed by a digit-select kernel), then an
+// emission pass of the documents above that score (fewer than k, so the list
+// cannot overflow again) and of the ties at it.  Every pass scores each
+// document identically (exact integer tail sums), so the four passes agree.
+// The grid is persistent: with no marked query every CTA returns at once.
+template <int IMPACT, int HK>
+gs_status launch_recover_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k,
+                           const DtConfig& c, const DtPlan& p, cudaStream_t s) {
+  using ST = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
+  const size_t smem = (size_t)c.G * c.T * (IMPACT == GS_IMPACT_U8 ? 4 : 8) + kDynSmemFixed;
+  int per_sm = 1;
+  gs_status st = tile_smem_attr<IMPACT, HK>(&per_sm);
+  if (st != GS_OK) return st;
+  const int sms = ix->sms > 0 ? ix->sms : 1;
+  const int tpc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)c.nt / (2 * (int64_t)sms)));
+  auto kr = dt_tile_kernel<IMPACT, kModeRecover, HK>;
+  DtRecover rec{p.ov_groups, p.n_ovg, p.q_over, p.ov_hist, p.ov_prefix, p.ov_theta, 0};
+  for (int pass = 0; pass < 4; ++pass) {
+    rec.pass = pass;
+    kr<<<sms * per_sm, kDtThreads, smem, s>>>(
+        ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
+        c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
+        p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, tpc, c.nt,
+        p.fixp, p.qscale, rec);
+    GS_LAUNCH_CHECK();
+    if (pass < 3) {
+      dt_over_select_kernel<ST><<<B, 1024, 0, s>>>(p.q_over, p.ov_hist, p.ov_prefix, p.ov_need, p.ov_theta, pass, k);
+      GS_LAUNCH_CHECK();
+    }
+  }
+  return GS_OK;
+}
+
 template <int IMPACT>
 gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
-                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
+                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s, bool recover) {
+  if (recover) {
+    if (c.HK == kHeadFma) return launch_recover_h<IMPACT, kHeadFma>(ix, q_indptr, B, q_nnz, k, c, p, s);
+    if (c.HK == kHeadTensor) return launch_recover_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, s);
+    return launch_recover_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, s);
+  }
   if (c.HK == kHeadFma) return launch_tiles_h<IMPACT, kHeadFma>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
   if (c.HK == kHeadTensor) return launch_tiles_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
   return launch_tiles_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
@@ -1219,15 +1490,18 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
                                        p.u_terms, p.u_ptr, p.n_u, p.ent, ix->head_slot, c.H, p.headw, p.head_act,
                                        p.head_nact, ix->max_abs, p.fixp, p.qscale, flags);
   GS_LAUNCH_CHECK();
-  GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, sizeof(uint32_t) * B, s));
+  GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, p.zero_bytes, s));
   GS_CUDA_TRY(cudaMemsetAsync(p.tiebm, 0, sizeof(uint32_t) * (size_t)B * c.bm_words, s));
   record_stage(opts, 1, s);
-  switch (ix->impact) {
-    case GS_IMPACT_F32: st = launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
-    case GS_IMPACT_F16: st = launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
-    case GS_IMPACT_BF16: st = launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
-    default: st = launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s); break;
-  }
+  auto tiles = [&](bool recover) {
+    switch (ix->impact) {
+      case GS_IMPACT_F32: return launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
+      case GS_IMPACT_F16: return launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
+      case GS_IMPACT_BF16: return launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
+      default: return launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
+    }
+  };
+  st = tiles(false);
   if (st != GS_OK) return st;
   if (c.R > 0) {
     dim3 grid((unsigned)std::min<int64_t>((c.sample_docs + 255) / 256, 64), (unsigned)B);
@@ -1239,13 +1513,31 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
                                                         p.cand_cnt, c.cap, p.tiebm, c.bm_words);
     GS_LAUNCH_CHECK();
   }
+  const DtOverflow ov{p.q_over, p.g_mark, p.n_ovg, p.ov_groups, p.ov_hist, p.tiebm, c.G};
   if (ix->impact == GS_IMPACT_U8)
-    dt_final_kernel<int32_t><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
-                                                c.R, k, out_ids, static_cast<int32_t*>(out_scores), flags);
+    dt_final_kernel<int32_t, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
+                                                       p.theta, c.R, k, out_ids, static_cast<int32_t*>(out_scores),
+                                                       flags, ov);
   else
-    dt_final_kernel<float><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
-                                              c.R, k, out_ids, static_cast<float*>(out_scores), flags);
+    dt_final_kernel<float, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
+                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov);
   GS_LAUNCH_CHECK();
+  // Without a sample every document is a candidate (cap >= N): no list can
+  // overflow.  With one, the queries the first final pass marked are
+  // recomputed exactly; with none marked these launches return at once.
+  if (c.R > 0) {
+    st = tiles(true);
+    if (st != GS_OK) return st;
+    if (ix->impact == GS_IMPACT_U8)
+      dt_final_kernel<int32_t, true><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
+                                                        p.ov_theta, 1, k, out_ids,
+                                                        static_cast<int32_t*>(out_scores), flags, ov);
+    else
+      dt_final_kernel<float, true><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
+                                                      p.ov_theta, 1, k, out_ids, static_cast<float*>(out_scores),
+                                                      flags, ov);
+    GS_LAUNCH_CHECK();
+  }
   record_stage(opts, 5, s);
   return GS_OK;
 }

@@ -24,7 +24,6 @@ __host__ __device__ constexpr int block_bytes(int impact) { return 128 + 32 * im
 constexpr uint32_t kFlagBadTerm = GS_FLAG_BAD_TERM;
 constexpr uint32_t kFlagBadWeight = GS_FLAG_BAD_WEIGHT;
 constexpr uint32_t kFlagCandOverflow = GS_FLAG_CAND_OVERFLOW;
-constexpr uint32_t kFlagTimeout = GS_FLAG_TIMEOUT;
 
 }  // namespace gs
 

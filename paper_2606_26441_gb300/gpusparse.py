@@ -21,7 +21,7 @@ GS_ERR_UNSUPPORTED, GS_ERR_DATA, GS_ERR_TIMEOUT, GS_ERR_WORKSPACE = 4, 5, 6, 7
 IMPACTS = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3}
 ALGOS = {"auto": 0, "term_parallel": 1, "doc_tiled": 2, "doc_parallel": 3}
 GS_FLAG_BAD_TERM, GS_FLAG_BAD_WEIGHT, GS_FLAG_CAND_OVERFLOW = 1, 2, 4
-GS_FLAG_TIMEOUT, GS_FLAG_BAD_INDPTR = 8, 16
+GS_FLAG_BAD_INDPTR = 16
 GS_MAX_K = 2048
 GS_STATIC_SCRATCH_BYTES = 64 << 20
 
