@@ -51,13 +51,15 @@ typedef enum {
   GS_ERR_OUT_OF_MEMORY = 2, /* index build could not allocate */
   GS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
   GS_ERR_UNSUPPORTED = 4,   /* valid but not supported (k > GS_MAX_K, ...) */
-  GS_ERR_DATA = 5,          /* invalid document data at index build */
+  GS_ERR_DATA = 5,          /* invalid document data at index build; from a
+                               synchronous search call: the device skipped
+                               invalid query data (GS_FLAG_BAD_*) */
   GS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
   GS_ERR_WORKSPACE = 7      /* workspace smaller than gs_search_workspace_size() */
 } gs_status;
 
 /* Stored impact type of the index (the paper stores float32, Sec. 3.2;
- * reduced precisions follow its future-work item 2, Sec. 7).
+ * reduced precisions follow its future-work item 2, Sec. 8).
  *   F32  : float32 impacts, float32 accumulation, float32 scores.
  *   F16  : IEEE binary16 impacts (nearest-even), float32 accumulation.
  *   BF16 : bfloat16 impacts (nearest-even), float32 accumulation.
@@ -74,7 +76,7 @@ typedef enum { GS_IMPACT_F32 = 0, GS_IMPACT_F16 = 1, GS_IMPACT_BF16 = 2, GS_IMPA
  *                   atomics; then a radix-select top-k over the rows.
  *   DOC_TILED     : a doc tile of the score rows of a group of queries lives
  *                   in shared memory; every (term, tile) posting segment is
- *                   read once per group (the hybrid kernel of Sec. 7, future
+ *                   read once per group (the hybrid kernel of Sec. 8, future
  *                   work 1).  Candidates above a per-query threshold taken
  *                   from a sampled subset of tiles are kept; the dense rows
  *                   are never written.
@@ -205,8 +207,15 @@ gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t* doc_terms,
                             int64_t num_docs, int64_t nnz, int32_t vocab, gs_impact impact,
                             const gs_build_opts* opts, gs_stream_t stream, gs_index** out);
 
+/* Sizes of the index (the block layout of Sec. 3.2, Eq. 2, and the memory
+ * accounting of Sec. 3.3: posting bytes = padded postings x (4 + impact
+ * bytes)).  Host call, no device work. */
 gs_status gs_index_info(const gs_index* index, gs_index_stats* out);
+/* Device addresses of the index arrays of Sec. 3.2 (see gs_index_layout);
+ * the views stay valid until gs_index_free. */
 gs_status gs_index_get_layout(const gs_index* index, gs_index_layout* out);
+/* Releases the index and all its device memory (Sec. 3.3's footprint);
+ * NULL is ignored.  No search on it may be in flight. */
 void gs_index_free(gs_index* index);
 
 /* --- search -------------------------------------------------------------- */
@@ -214,7 +223,10 @@ void gs_index_free(gs_index* index);
 /* Device workspace bytes gs_search / gs_score_dense need for a batch of
  * `batch` queries holding `q_nnz` terms in total, with top-`k` (k is
  * ignored by gs_score_dense).  opts may be NULL.  host_io != 0 adds room
- * for gs_search_host's device copies of the queries and results. */
+ * for gs_search_host's device copies of the queries and results.  This is
+ * the score-buffer memory of Sec. 7 (limitation 3): B x N score rows on the
+ * term-parallel path, per-query candidate lists and tie bitmaps on the
+ * doc-tiled path. */
 gs_status gs_search_workspace_size(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
                                    const gs_search_opts* opts, int32_t host_io, size_t* bytes);
 
@@ -243,7 +255,11 @@ gs_status gs_search(const gs_index* index, const int32_t* q_indptr, const int32_
 
 /* gs_search with the queries and results in host memory: copies the queries
  * to the workspace, searches, copies the results back and synchronises the
- * stream before returning.  The workspace must be sized with host_io = 1. */
+ * stream before returning.  The workspace must be sized with host_io = 1.
+ * Returns GS_ERR_DATA when the device skipped invalid query data (a flag of
+ * GS_FLAG_BAD_TERM, _BAD_WEIGHT or _BAD_INDPTR; gs_search_flags on the same
+ * workspace tells which); the results are written all the same, computed
+ * without the skipped terms. */
 gs_status gs_search_host(const gs_index* index, const int32_t* h_q_indptr, const int32_t* h_q_terms,
                          const float* h_q_w, int32_t batch, int64_t q_nnz, int32_t k,
                          int32_t* h_out_ids, void* h_out_scores, void* workspace,
@@ -291,7 +307,9 @@ gs_status gs_merge_topk(const int32_t* const* shard_ids, const void* const* shar
                         int32_t score_is_int, int32_t* out_ids, void* out_scores, gs_stream_t stream);
 
 /* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits the last
- * call that used `workspace` raised. */
+ * call that used `workspace` raised (the flag word leads the workspace; the
+ * data-error flags are those of the query checks of Sec. 4.2's batching step,
+ * the overflow flag that of the candidate lists). */
 gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags);
 
 /* --- uneven batches from captured CUDA graphs -----------------------------
@@ -311,6 +329,8 @@ typedef struct gs_runner gs_runner;
 
 gs_status gs_runner_create(const gs_index* index, int32_t max_batch, int64_t max_q_nnz, int32_t max_k,
                            const gs_search_opts* opts, int32_t autotune, gs_runner** out);
+/* Returns GS_ERR_DATA, with the results written, when the device skipped
+ * invalid query data (as gs_search_host does). */
 gs_status gs_runner_search(gs_runner* runner, const int32_t* h_q_indptr, const int32_t* h_q_terms,
                            const float* h_q_w, int32_t batch, int32_t k, int32_t* h_out_ids,
                            void* h_out_scores, gs_stream_t stream);
@@ -321,7 +341,7 @@ void gs_runner_free(gs_runner* runner);
 
 /* --- serving loop with continuous batching --------------------------------
  *
- * (Sec. 7, future work 3: streaming query batching.)  Requests — one query,
+ * (Sec. 8, future work 3: streaming query batching.)  Requests — one query,
  * its k, the index it targets — are submitted from any host thread and
  * queued.  A lane is one admission slot: a stream, a search workspace (the
  * score memory of one batch), device and pinned buffers; the number of lanes
@@ -361,12 +381,16 @@ typedef struct {
  * gs_server_destroy); index ids in requests are positions in this array. */
 gs_status gs_server_create(const gs_index* const* indexes, int32_t n_indexes, const gs_server_config* cfg,
                            gs_server** out);
-/* copies the query (host memory); *ticket identifies the request */
+/* copies the query (host memory); *ticket identifies the request.  A term id
+ * outside [0, V) of the target index or a non-finite weight is rejected here
+ * with GS_ERR_INVALID_ARG. */
 gs_status gs_server_submit(gs_server* server, int32_t index_id, const int32_t* terms, const float* weights,
                            int32_t nnz, int32_t k, int64_t* ticket);
 /* waits at most timeout_us for the request; on GS_OK writes k ids and k
  * scores (float32, int32 on uint8 indexes) to host memory and, when
- * latency_us is not NULL, the time from submit to completion */
+ * latency_us is not NULL, the time from submit to completion.  A batch whose
+ * search failed, or raised a data-error flag, gives each of its requests that
+ * status (GS_ERR_CUDA, GS_ERR_DATA). */
 gs_status gs_server_wait(gs_server* server, int64_t ticket, int32_t* out_ids, void* out_scores, int64_t timeout_us,
                          double* latency_us);
 gs_status gs_server_stats_get(gs_server* server, gs_server_stats* out);
@@ -395,16 +419,23 @@ void gs_server_destroy(gs_server* server);
  *     the GPU (other streams, other host threads) race on the array: serialise
  *     them.
  *   - It calls no cudaMalloc, cudaFree or allocating library routine.
- *   - gs_search_flags() takes the workspace pointer and therefore does not
- *     apply; data errors still skip the offending query terms. */
+ *   - Its flag word is read with gs_search_static_flags() (gs_search_flags()
+ *     takes a workspace pointer); data errors skip the offending query terms
+ *     as in gs_search. */
 #define GS_STATIC_SCRATCH_BYTES (64u << 20)
 
 gs_status gs_search_static(const gs_index* index, const int32_t* q_indptr, const int32_t* q_terms,
                            const float* q_w, int32_t batch, int64_t q_nnz, int32_t k, int32_t* out_ids,
                            void* out_scores, const gs_search_opts* opts, gs_stream_t stream);
 
-/* --- misc ---------------------------------------------------------------- */
+/* Synchronises `stream`, then returns in *flags the GS_FLAG_* bits that the
+ * last gs_search_static on the current device raised (the first word of the
+ * fixed scratch array).  Allocates nothing. */
+gs_status gs_search_static_flags(gs_stream_t stream, uint32_t* flags);
 
+/* --- misc (library plumbing; the paper has no counterpart) --------------- */
+
+/* a static string naming the status; never NULL */
 const char* gs_status_str(gs_status status);
 /* the CUDA error string of the last GS_ERR_CUDA on this host thread */
 const char* gs_last_cuda_error(void);

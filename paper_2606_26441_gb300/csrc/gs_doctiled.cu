@@ -1,5 +1,5 @@
 // Doc-tiled scoring with a sampled threshold (the hybrid kernel the paper
-// proposes as future work 1, Sec. 7: scatter-add work efficiency with
+// proposes as future work 1, Sec. 8: scatter-add work efficiency with
 // shared-memory accumulation), designed for sm_103a.
 //
 // The queries of a batch form groups of G consecutive queries; the documents

@@ -24,6 +24,8 @@ __host__ __device__ constexpr int block_bytes(int impact) { return 128 + 32 * im
 constexpr uint32_t kFlagBadTerm = GS_FLAG_BAD_TERM;
 constexpr uint32_t kFlagBadWeight = GS_FLAG_BAD_WEIGHT;
 constexpr uint32_t kFlagCandOverflow = GS_FLAG_CAND_OVERFLOW;
+// flags that report invalid query data (the informational overflow bit aside)
+constexpr uint32_t kDataFlags = GS_FLAG_BAD_TERM | GS_FLAG_BAD_WEIGHT | GS_FLAG_BAD_INDPTR;
 
 }  // namespace gs
 

@@ -37,6 +37,7 @@ struct gs_runner {
   int32_t* h_indptr = nullptr;
   int32_t* h_terms = nullptr;
   float* h_w = nullptr;
+  uint32_t* h_flags = nullptr;  // flag word of the last search
   // graphs are captured and replayed on the runner's own stream: capture is
   // not possible on the legacy default stream a caller may pass
   cudaStream_t own = nullptr;
@@ -174,6 +175,7 @@ void free_runner(gs_runner* r) {
   cudaFreeHost(r->h_indptr);
   cudaFreeHost(r->h_terms);
   cudaFreeHost(r->h_w);
+  cudaFreeHost(r->h_flags);
   if (r->dep) cudaEventDestroy(r->dep);
   if (r->own) cudaStreamDestroy(r->own);
   delete r;
@@ -218,6 +220,7 @@ extern "C" gs_status gs_runner_create(const gs_index* index, int32_t max_batch, 
       (e = cudaMallocHost(&r->h_indptr, sizeof(int32_t) * (B1 + 1))) != cudaSuccess ||
       (e = cudaMallocHost(&r->h_terms, sizeof(int32_t) * max_q_nnz)) != cudaSuccess ||
       (e = cudaMallocHost(&r->h_w, sizeof(float) * max_q_nnz)) != cudaSuccess ||
+      (e = cudaMallocHost(&r->h_flags, sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&r->own, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&r->dep, cudaEventDisableTiming)) != cudaSuccess) {
     gs::set_cuda_error(e);
@@ -267,8 +270,10 @@ extern "C" gs_status gs_runner_search(gs_runner* r, const int32_t* h_q_indptr, c
   GS_CUDA_TRY(cudaMemcpyAsync(h_out_ids, r->d_ids, sizeof(int32_t) * (size_t)batch * k, cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(
       cudaMemcpyAsync(h_out_scores, r->d_scores, sizeof(uint32_t) * (size_t)batch * k, cudaMemcpyDeviceToHost, s));
+  // the search's flag word leads the workspace
+  GS_CUDA_TRY(cudaMemcpyAsync(r->h_flags, r->ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaStreamSynchronize(s));
-  return GS_OK;
+  return (*r->h_flags & gs::kDataFlags) ? GS_ERR_DATA : GS_OK;
 }
 
 extern "C" gs_status gs_runner_plan(gs_runner* r, int32_t batch, int32_t k, gs_search_opts* out_opts,

@@ -442,8 +442,10 @@ extern "C" gs_status gs_search_host(const gs_index* ix, const int32_t* h_q_indpt
   if (st != GS_OK) return st;
   GS_CUDA_TRY(cudaMemcpyAsync(h_out_ids, io.ids, sizeof(int32_t) * B * (size_t)k, cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaMemcpyAsync(h_out_scores, io.scores, sizeof(uint32_t) * B * (size_t)k, cudaMemcpyDeviceToHost, s));
+  uint32_t flags = 0;  // the flag word leads the workspace
+  GS_CUDA_TRY(cudaMemcpyAsync(&flags, workspace, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaStreamSynchronize(s));
-  return GS_OK;
+  return (flags & kDataFlags) ? GS_ERR_DATA : GS_OK;
 }
 
 extern "C" gs_status gs_search_plan(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k,

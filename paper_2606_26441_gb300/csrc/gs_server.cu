@@ -1,5 +1,5 @@
 // Serving loop with continuous batching (the paper's future-work item 3,
-// Sec. 7: streaming query batching with adaptive accumulation).
+// Sec. 8: streaming query batching with adaptive accumulation).
 //
 // Requests (one sparse query, its k and its target index) are queued on the
 // host.  A lane is one admission slot: a CUDA stream, a search workspace
@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -62,6 +63,7 @@ struct Lane {
   float* h_w = nullptr;
   int32_t* h_ids = nullptr;
   uint32_t* h_scores = nullptr;
+  uint32_t* h_flags = nullptr;  // the batch's flag word
   // the batch in flight
   std::vector<std::shared_ptr<Request>> batch;
   int32_t batch_k = 0;
@@ -107,6 +109,7 @@ void free_lane(Lane* L) {
   cudaFreeHost(L->h_w);
   cudaFreeHost(L->h_ids);
   cudaFreeHost(L->h_scores);
+  cudaFreeHost(L->h_flags);
   if (L->done_ev) cudaEventDestroy(L->done_ev);
   if (L->stream) cudaStreamDestroy(L->stream);
 }
@@ -139,6 +142,7 @@ gs_status launch_batch(gs_server* S, Lane* L) {
   if (st != GS_OK) return st;
   GS_CUDA_TRY(cudaMemcpyAsync(L->h_ids, L->d_ids, sizeof(int32_t) * (size_t)B * k, cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaMemcpyAsync(L->h_scores, L->d_scores, sizeof(uint32_t) * (size_t)B * k, cudaMemcpyDeviceToHost, s));
+  GS_CUDA_TRY(cudaMemcpyAsync(L->h_flags, L->ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));  // flag word
   GS_CUDA_TRY(cudaEventRecord(L->done_ev, s));
   return GS_OK;
 }
@@ -207,6 +211,8 @@ void completer_loop(gs_server* S, Lane* L) {
       if (e != cudaSuccess) {
         gs::set_cuda_error(e);
         st = GS_ERR_CUDA;
+      } else if (*L->h_flags & gs::kDataFlags) {
+        st = GS_ERR_DATA;  // submit validates every query: not expected
       }
     }
     const auto now = Clock::now();
@@ -270,7 +276,8 @@ extern "C" gs_status gs_server_create(const gs_index* const* indexes, int32_t n_
         (e = cudaMallocHost(&L->h_indptr, 4 * (B + 1))) != cudaSuccess ||
         (e = cudaMallocHost(&L->h_terms, 4 * Q)) != cudaSuccess || (e = cudaMallocHost(&L->h_w, 4 * Q)) != cudaSuccess ||
         (e = cudaMallocHost(&L->h_ids, 4 * B * K)) != cudaSuccess ||
-        (e = cudaMallocHost(&L->h_scores, 4 * B * K)) != cudaSuccess) {
+        (e = cudaMallocHost(&L->h_scores, 4 * B * K)) != cudaSuccess ||
+        (e = cudaMallocHost(&L->h_flags, 4)) != cudaSuccess) {
       gs::set_cuda_error(e);
       free_lane(L.get());
       for (auto& l : S->lanes) free_lane(l.get());
@@ -292,6 +299,10 @@ extern "C" gs_status gs_server_submit(gs_server* S, int32_t index_id, const int3
       nnz > S->cfg.max_q_nnz || k < 1 || k > S->cfg.max_k || (nnz > 0 && (!terms || !weights)))
     return GS_ERR_INVALID_ARG;
   if ((int64_t)k > S->indexes[index_id]->N) return GS_ERR_INVALID_ARG;
+  // the query itself: term ids in [0, V) and finite weights
+  const int32_t V = S->indexes[index_id]->V;
+  for (int32_t i = 0; i < nnz; ++i)
+    if (terms[i] < 0 || terms[i] >= V || !std::isfinite(weights[i])) return GS_ERR_INVALID_ARG;
   auto r = std::make_shared<Request>();
   r->index_id = index_id;
   r->k = k;

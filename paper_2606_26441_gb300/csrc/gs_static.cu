@@ -58,3 +58,18 @@ extern "C" gs_status gs_search_static(const gs_index* index, const int32_t* q_in
   return gs_search(index, q_indptr, q_terms, q_w, batch, q_nnz, k, out_ids, out_scores, scratch,
                    (size_t)GS_STATIC_SCRATCH_BYTES, opts, stream);
 }
+
+extern "C" gs_status gs_search_static_flags(gs_stream_t stream, uint32_t* flags) {
+  if (!flags) return GS_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  gs_status st = scratch_for_current_device(&scratch);
+  if (st != GS_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(flags, scratch, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    gs::set_cuda_error(e);
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}

@@ -28,7 +28,7 @@ GS_STATIC_SCRATCH_BYTES = 64 << 20
 EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
-    "gs_search_plan", "gs_search_static", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
+    "gs_search_plan", "gs_search_static", "gs_search_static_flags", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
     "gs_runner_free", "gs_server_create", "gs_server_submit", "gs_server_wait", "gs_server_stats_get",
     "gs_server_destroy", "gs_merge_topk",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
@@ -56,7 +56,7 @@ class gs_index_stats(ctypes.Structure):
                 ("blocks", ctypes.c_int64), ("posting_bytes", ctypes.c_int64), ("meta_bytes", ctypes.c_int64),
                 ("vocab", ctypes.c_int32), ("impact", ctypes.c_int32), ("block_bytes", ctypes.c_int32),
                 ("tile_docs", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("score_is_int", ctypes.c_int32),
-                ("head_terms", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("head_bytes", ctypes.c_int64)]
+                ("head_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("head_bytes", ctypes.c_int64)]
 
 
 class gs_index_layout(ctypes.Structure):
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
     L.gs_search_plan.restype = ctypes.c_int
     L.gs_search_static.argtypes = [P, P, P, P, I32, I64, I32, P, P, ctypes.POINTER(gs_search_opts), P]
     L.gs_search_static.restype = ctypes.c_int
+    L.gs_search_static_flags.argtypes = [P, ctypes.POINTER(ctypes.c_uint32)]
+    L.gs_search_static_flags.restype = ctypes.c_int
     L.gs_runner_create.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), I32, ctypes.POINTER(P)]
     L.gs_runner_create.restype = ctypes.c_int
     L.gs_runner_search.argtypes = [P, P, P, P, I32, I32, P, P, P]
@@ -344,7 +346,10 @@ def gs_search_static(index: Index, q: Queries, k: int, opts=None, out_ids=None, 
 
 def gs_search_host(index: Index, h_indptr, h_terms, h_w, k: int, out_ids, out_scores, workspace, opts=None,
                    stream=None):
-    """Host-memory queries and results (tensors on the CPU, ideally pinned); synchronous."""
+    """Host-memory queries and results (tensors on the CPU, ideally pinned); synchronous.
+
+    Raises GsError(GS_ERR_DATA) when the device skipped invalid query data; the results are
+    written all the same (gs_search_flags(workspace) tells which flags were raised)."""
     L = load()
     B = h_indptr.numel() - 1
     _check(L.gs_search_host(index.handle, _ptr(h_indptr), _ptr(h_terms), _ptr(h_w), B, h_terms.numel(), k,
@@ -365,6 +370,14 @@ def gs_score_dense(index: Index, q: Queries, workspace=None, stream=None) -> tor
     _check(L.gs_score_dense(index.handle, _ptr(q.indptr), _ptr(q.terms), _ptr(q.weights), q.batch, q.nnz,
                             _ptr(rows), _ptr(workspace), workspace.numel(), _stream(stream)), "gs_score_dense")
     return rows
+
+
+def gs_search_static_flags(stream=None) -> int:
+    """Synchronises the stream and returns the GS_FLAG_* bits of the last gs_search_static on this device."""
+    L = load()
+    f = ctypes.c_uint32(0)
+    _check(L.gs_search_static_flags(_stream(stream), ctypes.byref(f)), "gs_search_static_flags")
+    return int(f.value)
 
 
 def gs_search_flags(workspace: torch.Tensor, stream=None) -> int:

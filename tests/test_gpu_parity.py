@@ -309,6 +309,42 @@ def test_fixed_point_tail_coarse_scale():
         c.idx.free()
 
 
+@pytest.mark.parametrize("algo,kw", VARIANTS)
+@pytest.mark.parametrize("impact", ["f32", "f16", "bf16", "u8"])
+def test_handworked_golden_on_gpu(impact, algo, kw):
+    """The hand-worked example of tests/golden (Sec. 4.1 Eq. 4 by hand: ties broken by id,
+    u8 half-way quantisation 0.5 -> 26 and 1.5 -> 76, a negative weight, a repeated term,
+    an empty query, an absent term) through the C ABI.  Its values are dyadic, exact in
+    every impact type, so the GPU must reproduce the stored scores and order exactly."""
+    import json
+    import os
+    gs = _gs()
+    dev = _dev()
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "handworked.json")))
+    rows = [sorted((int(t), float(w)) for t, w in d.items()) for d in g["docs"]]
+    indptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    terms = np.array([t for r in rows for t, _ in r], np.int32)
+    weights = np.array([w for r in rows for _, w in r], np.float32)
+    idx = gs.gs_index_build(torch.from_numpy(indptr).to(dev), torch.from_numpy(terms).to(dev),
+                            torch.from_numpy(weights).to(dev), g["vocab"], impact, 256, 0, True)
+    try:
+        qind = np.cumsum([0] + [len(q["terms"]) for q in g["queries"]]).astype(np.int32)
+        qt = np.array([t for q in g["queries"] for t in q["terms"]], np.int32)
+        qw = np.array([w for q in g["queries"] for w in q["weights"]], np.float32)
+        q = gs.Queries.from_numpy(qind, qt, qw, dev)
+        n = len(rows)
+        for k in (n, 2):
+            ids, sc = gs.gs_search(idx, q, k, gs.make_opts(algo, **kw))
+            ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+            for i, qq in enumerate(g["queries"]):
+                want = qq["u8" if impact == "u8" else "f32"]
+                order = want["order"][:k]
+                assert ids[i].tolist() == order, (qq["name"], ids[i].tolist(), order)
+                assert [float(x) for x in sc[i]] == [float(want["scores"][d]) for d in order], qq["name"]
+    finally:
+        idx.free()
+
+
 def test_bad_query_terms_are_flagged():
     gs = _gs()
     docs = synth.docs(3_000, seed=4)
@@ -326,6 +362,59 @@ def test_bad_query_terms_are_flagged():
         assert flags & gs.GS_FLAG_BAD_TERM
         assert flags & gs.GS_FLAG_BAD_WEIGHT
         check.check_float(c.ref, bad.indptr, bad.terms, bad.weights, ids, sc, ref_ids, ref_sc, docs.n)
+    # synchronous calls report the skipped data with GS_ERR_DATA (results written all the same)
+    k = 5
+    opts = gs.make_opts("doc_tiled")
+    ws = gs.alloc_workspace(c.idx, bad.n, bad.nnz, k, opts, host_io=True)
+    h_ids = torch.empty((bad.n, k), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((bad.n, k), dtype=torch.float32).pin_memory()
+    h = (torch.from_numpy(bad.indptr.astype(np.int32)), torch.from_numpy(bad.terms), torch.from_numpy(bad.weights))
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_search_host(c.idx, *h, k, h_ids, h_sc, ws, opts)
+    assert e.value.status == gs.GS_ERR_DATA
+    assert gs.gs_search_flags(ws) == gs.GS_FLAG_BAD_TERM | gs.GS_FLAG_BAD_WEIGHT
+    check.check_float(c.ref, bad.indptr, bad.terms, bad.weights, h_ids.numpy(), h_sc.numpy(), ref_ids, ref_sc,
+                      docs.n)
+    runner = gs.Runner(c.idx, max_batch=4, max_q_nnz=bad.nnz, max_k=k, autotune=False)
+    with pytest.raises(gs.GsError) as e:
+        runner.search(*h, k)
+    assert e.value.status == gs.GS_ERR_DATA
+    runner.free()
+    # the server rejects such a request at submit
+    server = gs.Server([c.idx], lanes=1, max_batch=4, max_q_nnz=256, max_k=k)
+    t0, w0 = bad.row(0)
+    with pytest.raises(gs.GsError) as e:
+        server.submit(0, np.ascontiguousarray(t0), np.ascontiguousarray(w0), k)
+    assert e.value.status == gs.GS_ERR_INVALID_ARG
+    t3, w3 = bad.row(3)
+    with pytest.raises(gs.GsError):
+        server.submit(0, np.ascontiguousarray(t3), np.ascontiguousarray(w3), k)
+    server.close()
+
+
+def test_query_row_pointer_past_capacity_is_flagged():
+    """A query CSR whose row pointer ends past q_nnz raises GS_FLAG_BAD_INDPTR; every
+    access stays inside the first q_nnz entries (the arrays here hold more)."""
+    gs = _gs()
+    dev = _dev()
+    docs = synth.docs(5_000, seed=11)
+    qs = synth.queries(6, seed=11)
+    c = Case(docs, qs, "f32", tile_docs=256)
+    L = gs.load()
+    k = 5
+    for algo in ALGOS:
+        opts = gs.make_opts(algo)
+        short = qs.nnz - 3  # the row pointer ends 3 entries past this capacity
+        ws = gs.alloc_workspace(c.idx, qs.n, short, k, opts)
+        ids = torch.empty((qs.n, k), dtype=torch.int32, device=dev)
+        sc = torch.empty((qs.n, k), dtype=torch.float32, device=dev)
+        st = L.gs_search(c.idx.handle, ctypes.c_void_p(c.q.indptr.data_ptr()), ctypes.c_void_p(c.q.terms.data_ptr()),
+                         ctypes.c_void_p(c.q.weights.data_ptr()), qs.n, short, k, ctypes.c_void_p(ids.data_ptr()),
+                         ctypes.c_void_p(sc.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                         ctypes.byref(opts), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == gs.GS_OK
+        assert gs.gs_search_flags(ws) & gs.GS_FLAG_BAD_INDPTR
+    c.idx.free()
 
 
 def test_argument_errors():
@@ -423,19 +512,21 @@ def test_reduced_precision_error_vs_fp64():
 @pytest.mark.slow
 def test_full_size_batch_sampled_rows():
     """The bench's workload and launch: 8,841,823 documents, one batch of 500
-    queries, top-1000, default doc-tiled plan.  The oracle checks a sample of the
-    returned rows (every 32nd query: one per query group), uint8 bit-exact and
-    FP32 / FP16 within tau."""
+    queries, top-1000, default doc-tiled plan (groups of 16 queries).  The oracle
+    checks one returned row of every query group, at a different position in
+    each group (row 16 g + g mod the group's size), uint8 bit-exact and FP32 / FP16 / BF16
+    within tau."""
     import os
     docs = synth.docs(synth.N_8_8M, seed=0, threads=os.cpu_count() or 0)
     qs = synth.queries(500, seed=0)
     k = 1000
-    rows = np.arange(0, qs.n, 32)
+    rows = np.array([16 * g + g % min(16, qs.n - 16 * g) for g in range((qs.n + 15) // 16)])
+    assert len(rows) == 32 and rows[-1] < qs.n
     parts = [qs.slice(int(r), int(r) + 1) for r in rows]
     indptr = np.cumsum([0] + [p.nnz for p in parts]).astype(np.int64)
     sample = synth.SparseBatch(indptr, np.concatenate([p.terms for p in parts]),
                                np.concatenate([p.weights for p in parts]))
-    for impact in ("u8", "f32", "f16"):
+    for impact in ("u8", "f32", "f16", "bf16"):
         c = Case(docs, qs, impact)
         ids, sc, flags = c.search(k, "doc_tiled")
         assert flags == 0
