@@ -386,9 +386,16 @@ def test_bad_query_terms_are_flagged():
     with pytest.raises(gs.GsError) as e:
         server.submit(0, np.ascontiguousarray(t0), np.ascontiguousarray(w0), k)
     assert e.value.status == gs.GS_ERR_INVALID_ARG
-    t3, w3 = bad.row(3)
-    with pytest.raises(gs.GsError):
-        server.submit(0, np.ascontiguousarray(t3), np.ascontiguousarray(w3), k)
+    qn = int(np.searchsorted(bad.indptr, 3, side="right") - 1)  # the query holding the NaN weight
+    tn, wn = bad.row(qn)
+    assert np.isnan(wn).any()
+    with pytest.raises(gs.GsError) as e:
+        server.submit(0, np.ascontiguousarray(tn), np.ascontiguousarray(wn), k)
+    assert e.value.status == gs.GS_ERR_INVALID_ARG
+    t1, w1 = bad.row(1)  # a valid request is served
+    ids1, sc1, _ = server.wait(server.submit(0, np.ascontiguousarray(t1), np.ascontiguousarray(w1), k), k,
+                               torch.float32)
+    assert ids1.tolist() == ref_ids[1].tolist()
     server.close()
 
 
