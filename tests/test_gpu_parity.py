@@ -392,10 +392,14 @@ def test_bad_query_terms_are_flagged():
     with pytest.raises(gs.GsError) as e:
         server.submit(0, np.ascontiguousarray(tn), np.ascontiguousarray(wn), k)
     assert e.value.status == gs.GS_ERR_INVALID_ARG
-    t1, w1 = bad.row(1)  # a valid request is served
-    ids1, sc1, _ = server.wait(server.submit(0, np.ascontiguousarray(t1), np.ascontiguousarray(w1), k), k,
+    qv = next(i for i in range(bad.n) if bad.indptr[i] > 3 or bad.indptr[i + 1] <= 0)  # a valid query
+    tv, wv = bad.row(qv)
+    assert np.all(tv < docs.vocab) and np.all(np.isfinite(wv))
+    ids1, sc1, _ = server.wait(server.submit(0, np.ascontiguousarray(tv), np.ascontiguousarray(wv), k), k,
                                torch.float32)
-    assert ids1.tolist() == ref_ids[1].tolist()
+    one = bad.slice(qv, qv + 1)
+    check.check_float(c.ref, one.indptr, one.terms, one.weights, ids1[None], sc1[None], ref_ids[qv:qv + 1],
+                      ref_sc[qv:qv + 1], docs.n)
     server.close()
 
 
