@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
         const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
         uint32_t hi[4], lo[4];
-  #pragma unroll
+#pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int q = gid + 8 * (e & 1);
           const int a = 8 * ks + tig + 4 * (e >> 1);
@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       }
     }
 
+    bool need_clear = true;
     for (int tile_idx = tile_begin; tile_idx < tile_end; ++tile_idx) {
       int tau;
       if (MODE == kModeSample) {
@@ -564,9 +565,12 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       const int64_t doc0 = (int64_t)tau * T;
       const int seg_lo = tau * m, seg_hi = min((tau + 1) * m, seg_tiles);
       __syncthreads();  // the previous tile's rows are no longer read
-      {
+      // the first tile of a unit clears the block; the sample and main
+      // epilogues then clear each row as they finish reading it
+      if (need_clear || MODE == kModeRecover) {
         uint4* a4 = reinterpret_cast<uint4*>(acc);
         for (int i = threadIdx.x; i < G * T * kCell / 16; i += blockDim.x) a4[i] = make_uint4(0, 0, 0, 0);
+        need_clear = false;
       }
       // the planning scan's barriers order the clearing before the tail's
       // reductions; a group without tail terms needs one before the head
@@ -643,9 +647,9 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           const uint8_t* base = s_p0[jj] + (uint32_t)(4 * c * bb);
           const int rel = 128 * c + lane - s_off[jj];  // segment position of this lane's posting in block 0
           const uint32_t len = (uint32_t)s_len[jj];
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < 4; ++i) {
-            da[i] = -1;
+            da[i] = lane * kCell;  // no posting: a zero is added to cell `lane` of the row
             x[i] = (AccT)0;
             if ((uint32_t)(rel + 32 * i) < len) {
               const uint8_t* blk = base + i * bb;
@@ -658,14 +662,16 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           return jj;
         };
         // NI loaded items of term jj: every entry of the term, every posting
-        auto score_items = [&](auto fxc, int jj, const int* da, const AccT* x, int ni) {
+        // (a lane without a posting adds zero to cell `lane`, so the loop
+        // needs no predicate)
+        auto score_items = [&](auto fxc, auto ni_c, int jj, const int* da, const AccT* x) {
+          constexpr int NI = decltype(ni_c)::value;
           const int32_t eb = s_e0[jj], ee = s_e0[jj + 1];
           for (int32_t en = eb; en < ee; ++en) {
             const uint2 E = entry(en);
             const uint32_t row = acc_s + E.x;
-  #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (i < 4 * ni && da[i] >= 0) red(fxc, row + (uint32_t)da[i], E.y, x[i]);
+#pragma unroll
+            for (int i = 0; i < 4 * NI; ++i) red(fxc, row + (uint32_t)da[i], E.y, x[i]);
           }
         };
         // 32 postings of the packed short segments: one posting per lane, its
@@ -705,10 +711,10 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               const int ja = load_item(it, da, x);
               const int jb = load_item(it + 1, da + 4, x + 4);
               if (ja == jb) {
-                score_items(fxc, ja, da, x, 2);  // consecutive chunks of one segment: one pass over the entries
+                score_items(fxc, std::integral_constant<int, 2>{}, ja, da, x);  // consecutive chunks of one segment
               } else {
-                score_items(fxc, ja, da, x, 1);
-                score_items(fxc, jb, da + 4, x + 4, 1);
+                score_items(fxc, std::integral_constant<int, 1>{}, ja, da, x);
+                score_items(fxc, std::integral_constant<int, 1>{}, jb, da + 4, x + 4);
               }
             } else {
               for (int u = it; u < min(it + 2, units); ++u) {
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                   int da[4];
                   AccT x[4];
                   const int jj = load_item(u, da, x);
-                  score_items(fxc, jj, da, x, 1);
+                  score_items(fxc, std::integral_constant<int, 1>{}, jj, da, x);
                 } else {
                   score_packed(fxc, u);
                 }
@@ -770,7 +776,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
             if (slab + 2 * dp >= T) break;  // tiles shorter than one slab
             const int64_t col = doc0 + slab + 2 * dp;
             AccT r[16][2];
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = (AccT)0;
             auto load2 = [&](int a, AccT& x0, AccT& x1) {
               const int64_t at = (int64_t)s_hact[a] * head_ld + col;
@@ -793,20 +799,20 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
             };
             for (int a0 = 0; a0 < nact; a0 += 4) {
               AccT xs[4][2];
-  #pragma unroll
+#pragma unroll
               for (int u = 0; u < 4; ++u) {
                 xs[u][0] = xs[u][1] = (AccT)0;
                 if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
               }
-  #pragma unroll
+#pragma unroll
               for (int u = 0; u < 4; ++u) {
                 if (a0 + u >= nact) break;
                 const AccT* wr = s_w + (a0 + u) * kHeadG;
-  #pragma unroll
+#pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
                   AccT w4[4];
                   *reinterpret_cast<uint4*>(w4) = *reinterpret_cast<const uint4*>(wr + 4 * q4);
-  #pragma unroll
+#pragma unroll
                   for (int v = 0; v < 4; ++v) {
                     if (IMPACT == GS_IMPACT_U8) {
                       r[4 * q4 + v][0] += w4[v] * xs[u][0];
@@ -819,7 +825,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                 }
               }
             }
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 16; ++i) {
               const int q = i;
               if (q < gq) {
@@ -858,20 +864,20 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           for (int cb = warp * 8 * NT; cb < T; cb += kDtThreads / 32 * 8 * NT) {
             const int64_t col = doc0 + cb + NT * gid;
             float d[NT][4];
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < NT; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
             for (int k0 = 0; k0 < KS; k0 += KB) {
               VecT xv[KB][2];  // rows 8 ks + tig and 8 ks + tig + 4, NT documents each
-  #pragma unroll
+#pragma unroll
               for (int u = 0; u < KB; ++u)
-  #pragma unroll
+#pragma unroll
                 for (int h = 0; h < 2; ++h) {
                   const int r = 8 * (k0 + u) + tig + 4 * h;
                   xv[u][h] = VecT{};
                   if (r < nact)
                     xv[u][h] = __ldg(reinterpret_cast<const VecT*>(head_dense + ((int64_t)s_hact[r] * head_ld + col) * ib));
                 }
-  #pragma unroll
+#pragma unroll
               for (int u = 0; u < KB; ++u) {
                 if (k0 + u >= KS) break;
                 const uint4 ah = s_af[2 * ((k0 + u) * 32 + lane)];
@@ -881,7 +887,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                   const uint4 al = s_af[2 * ((k0 + u) * 32 + lane) + 1];
                   a_lo[0] = al.x; a_lo[1] = al.y; a_lo[2] = al.z; a_lo[3] = al.w;
                 }
-  #pragma unroll
+#pragma unroll
                 for (int j = 0; j < NT; ++j) {
                   if constexpr (IMPACT == GS_IMPACT_F32) {
                     // x = high + low TF32 parts as well: three products
@@ -900,11 +906,11 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               }
             }
             // D: (query gid + 8 h, document cb + 2 NT tig + NT c + j) = d[j][2 h + c]
-  #pragma unroll
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int q = gid + 8 * h;
               if (q >= gq) continue;
-  #pragma unroll
+#pragma unroll
               for (int c = 0; c < 2; ++c) {
                 AccT* dst = acc + q * T + cb + 2 * NT * tig + NT * c;
                 if constexpr (IMPACT == GS_IMPACT_U8) {
@@ -935,20 +941,20 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
             if (slab + 2 * dp >= T) break;
             const int64_t col = doc0 + slab + 2 * dp;
             int32_t r[16][2];
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 16; ++i) r[i][0] = r[i][1] = 0;
             for (int a = 0; a < nact; ++a) {
               const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(head_dense + (int64_t)s_hact[a] * head_ld + col));
               const int32_t x0 = v & 0xff, x1 = v >> 8;
               const uint32_t* wr = headw + ((int64_t)g * H + s_hact[a]) * kHeadG;
-  #pragma unroll
+#pragma unroll
               for (int i = 0; i < 16; ++i) {
                 const int32_t w = (int32_t)__ldg(wr + i);
                 r[i][0] += w * x0;
                 r[i][1] += w * x1;
               }
             }
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 16; ++i) {
               if (i < gq) {
                 int2* dst = reinterpret_cast<int2*>(acc + i * T + slab + 2 * dp);
@@ -976,6 +982,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           const int d0 = (ci - ql * cpr) * 128 + lane * 4;
           *reinterpret_cast<uint4*>(samp + (int64_t)(q0 + ql) * sample_docs + (int64_t)tile_idx * T + d0) =
               *reinterpret_cast<const uint4*>(acc + ql * T + d0);
+          *reinterpret_cast<uint4*>(acc + ql * T + d0) = make_uint4(0, 0, 0, 0);
         }
         continue;
       }
@@ -1023,13 +1030,13 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           // split into candidates (> theta_q) and ties (== theta_q)
           uint32_t ge_bits = 0;
           const int nc = min(8, (T - w0) / 128);
-  #pragma unroll
+#pragma unroll
           for (int c = 0; c < 8; ++c) {
             if (c >= nc) break;
             const int d0 = w0 + c * 128 + lane * 4;
             const uint4 raw = *reinterpret_cast<const uint4*>(row + d0);
             const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 4; ++i) {
               bool ge;
               if (IMPACT == GS_IMPACT_U8) ge = (int32_t)rv[i] >= (int32_t)th;
@@ -1040,9 +1047,9 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           if (n_in < (int64_t)(w0 + 1024)) {
             // the collection ends inside this window: drop documents >= N
             uint32_t keep = 0;
-  #pragma unroll
+#pragma unroll
             for (int c = 0; c < 8; ++c)
-  #pragma unroll
+#pragma unroll
               for (int i = 0; i < 4; ++i) keep |= (uint32_t)((int64_t)(w0 + c * 128 + lane * 4 + i) < n_in) << (4 * c + i);
             ge_bits &= keep;
           }
@@ -1061,7 +1068,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           }
           const int n_gt = __popc(gt_bits);
           int incl = n_gt;
-  #pragma unroll
+#pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
@@ -1091,6 +1098,10 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
               if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + (wdoc >> 5)] = word;
             }
           }
+        }
+        if (MODE == kModeMain) {  // the row is read: clear it for the next tile
+          __syncwarp();
+          for (int d0 = lane * 4; d0 < T; d0 += 128) *reinterpret_cast<uint4*>(acc + ql * T + d0) = make_uint4(0, 0, 0, 0);
         }
       }
     }
