@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0 = one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the serving and uneven-batch legs")
+    ap.add_argument("--microbench", action="store_true",
+                    help="build and run the rate microbenchmarks (paper_2606_26441_gb300/microbench/rates.cu)")
     return ap.parse_args()
 
 
@@ -238,7 +241,7 @@ def naive_stream_bytes(docs, qs, impact, df):
 
 
 def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
-    """Algorithmic bytes of the dominant kernel per launch (see DESIGN.md).
+    """Algorithmic bytes of the dominant kernel per launch.
 
     doc_tiled main pass : sum over groups of sum over the group's distinct terms
                           of the term's postings outside the sample tiles,
@@ -262,6 +265,46 @@ def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
     return post * b, {"postings": post}
 
 
+MICROBENCH_FILE = os.path.join(ROOT, "profiles", "microbench_shared_red_ffma_l2_red.md")
+
+
+def microbench_rates():
+    """Measured rates committed in the microbenchmark summary: {name: per-clock-per-SM value}."""
+    out = {}
+    if not os.path.exists(MICROBENCH_FILE):
+        return out
+    for line in open(MICROBENCH_FILE):
+        if line.startswith("- ") and ": " in line:
+            key, val = line[2:].split(": ", 1)
+            try:
+                out[key.strip()] = float(val.strip().split()[0])
+            except ValueError:
+                pass
+    return out
+
+
+def compute_work(plan, docs, qs, df, sample_df, head_terms):
+    """Work of the doc-tiled main pass that is not HBM traffic: shared-memory
+    reductions of the sparse tail (one per (query, posting) of a non-head term
+    outside the sample tiles) and FMAs of the dense head (16 queries x the
+    group's active head rows x every document of the main tiles)."""
+    H = head_terms
+    head = set(np.argsort(-df, kind="stable")[:H].tolist()) if H > 0 else set()
+    main_df = df - sample_df
+    n_main = docs.n - plan.sample_tiles * plan.tile_docs
+    G = plan.group_queries
+    tail = 0
+    head_rows = 0
+    for g0 in range(0, qs.n, G):
+        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
+        t = qs.terms[a:e]
+        in_head = np.isin(t, list(head)) if head else np.zeros(t.shape, bool)
+        tail += int(main_df[t[~in_head]].sum())
+        head_rows += len(np.unique(t[in_head]))
+    head_flops = 2 * 16 * head_rows * n_main if H > 0 else 0
+    return tail, head_flops
+
+
 def sample_term_counts(docs, T, R, n_sample):
     """Postings of every term inside the sample tiles (tiles j * R, j < n_sample)."""
     cnt = np.zeros(docs.vocab, dtype=np.int64)
@@ -272,6 +315,12 @@ def sample_term_counts(docs, T, R, n_sample):
         a, e = int(docs.indptr[d0]), int(docs.indptr[min(docs.n, d0 + T)])
         cnt += np.bincount(docs.terms[a:e], minlength=docs.vocab)
     return cnt
+
+
+def check_flags(gs, flags, when):
+    bad = flags & (gs.GS_FLAG_BAD_TERM | gs.GS_FLAG_BAD_WEIGHT | gs.GS_FLAG_BAD_INDPTR)
+    if bad:
+        raise RuntimeError(f"search raised data flags {bad} ({when})")
 
 
 def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sample_clocks=False, opts_kw=None):
@@ -288,9 +337,7 @@ def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sam
     out_sc = torch.empty((q.batch, k), dtype=idx.score_dtype, device=q.indptr.device)
     for _ in range(warmup):
         gs.gs_search(idx, q, k, opts_plain, ws, out_ids, out_sc)
-    flags = gs.gs_search_flags(ws)
-    if flags:
-        raise RuntimeError(f"search raised flags {flags}")
+    check_flags(gs, gs.gs_search_flags(ws), "warm-up")
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -312,11 +359,16 @@ def time_form(gs, torch, idx, q, k, algo, steps, warmup, dist, device_index, sam
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # the flag word of the last timed search: invalid query data fails the run;
+    # a candidate overflow (results exact, recomputed) is reported
+    flags = gs.gs_search_flags(ws)
+    check_flags(gs, flags, "timed steps")
     per_step = [e[0].elapsed_time(e[-1]) for e in ev]
     span = ev[0][0].elapsed_time(ev[-1][-1])
     stages = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(len(e) - 1)] for e in ev])
     return {"span_ms": span, "per_step_ms": per_step, "stage_ms": stages.mean(axis=0).tolist(), "wall_s": wall,
-            "launches": launches, "clocks": clocks, "ids": out_ids, "scores": out_sc, "ws": ws}
+            "launches": launches, "clocks": clocks, "ids": out_ids, "scores": out_sc, "ws": ws,
+            "cand_overflow": bool(flags & gs.GS_FLAG_CAND_OVERFLOW)}
 
 
 def e2e_form(gs, torch, idx, qs, k, algo, steps, warmup):
@@ -402,7 +454,8 @@ def run_gpu(args, w, docs, qs, world, rank, local):
             "p99_ms": float(np.percentile(ms, 99)), "per_query_ms": float(np.mean(ms)) / w.batch,
             "stage_ms": dict(zip(stage_names if algo == "doc_tiled" else
                                  ["query_prep", "zero_rows", "-", "scoring", "topk"], rr["stage_ms"])),
-            "index_bytes": int(ix.stats().posting_bytes), "meta_bytes": int(ix.stats().meta_bytes)}
+            "index_bytes": int(ix.stats().posting_bytes), "meta_bytes": int(ix.stats().meta_bytes),
+            "cand_overflow": rr["cand_overflow"]}
     plain = forms_out.get("f32:term_parallel")
     out = {
         "metric": METRIC, "value": value, "unit": "QPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -426,12 +479,99 @@ def run_gpu(args, w, docs, qs, world, rank, local):
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }
+    rf = out["roofline"]
+    if rf["traffic"]:
+        # measured DRAM bytes over the same launch time: how much of HBM the pass really uses
+        rf["dram_gbs"] = rf["traffic"] / (kern_ms / 1e3) / 1e9
+        rf["dram_frac"] = rf["dram_gbs"] / peak
+    if head_algo == "doc_tiled":
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
+        rates = microbench_rates()
+        tail, head_flops = compute_work(plan, docs, qs, df, layout_info["sample_df"], st.head_terms)
+        comp = {"sm_mhz": mhz, "sms": sms, "tail_reductions": tail,
+                "tail_reductions_per_s": tail / (kern_ms / 1e3), "head_flops": head_flops,
+                "head_tflops": head_flops / (kern_ms / 1e3) / 1e12,
+                "source": os.path.relpath(MICROBENCH_FILE, ROOT)}
+        red = rates.get("red.shared.add.s32 random cells, lanes per clk per SM")
+        if red:
+            comp["red_shared_peak_per_s"] = red * sms * mhz * 1e6
+            comp["tail_frac"] = comp["tail_reductions_per_s"] / comp["red_shared_peak_per_s"]
+        ffma = rates.get("ffma, FMA lanes per clk per SM")
+        if ffma:
+            comp["ffma_peak_tflops"] = 2 * ffma * sms * mhz * 1e6 / 1e12
+            comp["head_frac"] = comp["head_tflops"] / comp["ffma_peak_tflops"]
+        rf["compute"] = comp
     if not args.no_e2e:
         out["e2e"] = e2e_form(gs, torch, idx, qs, k, head_algo, max(3, args.steps // 2), 2)
+    if not args.no_legs and world == 1:
+        out["serving"] = serving_leg(gs, torch, dev, docs, d_indptr, d_terms, d_w, indexes, forms_out)
+        out["uneven"] = uneven_leg(gs, torch, indexes.get("f32") or idx, docs)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def uneven_point(gs, torch, idx, runner, qs, B, k, steps, max_nnz):
+    """One (batch size, k) point of the uneven-batch suite: the same host batches through
+    plain per-batch gs_search_host calls (default plan, no graph) and through the
+    runner's autotuned, graph-replayed plan.  Host queries in, host results out."""
+    subs = [qs.slice(i * B, (i + 1) * B) for i in range(steps + 1)]
+    host = [(torch.from_numpy(sb.indptr.astype(np.int32)).pin_memory(), torch.from_numpy(sb.terms).pin_memory(),
+             torch.from_numpy(sb.weights).pin_memory()) for sb in subs]
+    opts = gs.make_opts("auto")
+    ws = gs.alloc_workspace(idx, B, max_nnz, k, opts, host_io=True)
+    hid = torch.empty((B, k), dtype=torch.int32).pin_memory()
+    hsc = torch.empty((B, k), dtype=idx.score_dtype).pin_memory()
+    t_plain = []
+    for i, (a, b, c) in enumerate(host):
+        t = time.perf_counter()
+        gs.gs_search_host(idx, a, b, c, k, hid, hsc, ws, opts)
+        if i:
+            t_plain.append((time.perf_counter() - t) * 1e3)
+    del ws
+    t_graph = []
+    for i, (a, b, c) in enumerate(host):
+        t = time.perf_counter()
+        runner.search(a, b, c, k, hid, hsc)
+        if i:  # the first call tunes and captures
+            t_graph.append((time.perf_counter() - t) * 1e3)
+    row = {"batch": B, "k": k}
+    for name, ts in (("plain", t_plain), ("graph_tuned", t_graph)):
+        row[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                     "qps": B * len(ts) / (sum(ts) / 1e3)}
+    row["plan"] = runner.plan(B, k)
+    row["speedup"] = row["plain"]["p50_ms"] / row["graph_tuned"]["p50_ms"]
+    return row
+
+
+UNEVEN_LAW = "70% Poisson(20), 25% Poisson(60), 5% uniform[150,300], clamped [1,300]"
+
+
+def uneven_suite(gs, torch, idx, points, steps):
+    batches = sorted({B for B, _ in points})
+    need = max(batches) * (steps + 2)
+    qs = synth.queries(need, seed=0, law=synth.MIXTURE_LAW)
+    max_nnz = max(int(qs.indptr[i + max(batches)] - qs.indptr[i])
+                  for i in range(0, need - max(batches) + 1, max(batches)))
+    runner = gs.Runner(idx, max_batch=max(batches), max_q_nnz=max_nnz, max_k=max(k for _, k in points))
+    rows = []
+    for B, k in points:
+        rows.append(uneven_point(gs, torch, idx, runner, qs, B, k, steps, max_nnz))
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    runner.free()
+    return rows
+
+
+def uneven_leg(gs, torch, idx, docs):
+    """Bounded leg of the default run: batch 1 (k = 10) and batch 64 (k = 1000) of
+    mixture-law queries on the headline's FP32 index."""
+    t0 = time.perf_counter()
+    rows = uneven_suite(gs, torch, idx, [(1, 10), (64, 1000)], steps=8)
+    return {"metric": "p50/p99 batch latency, graph-replayed autotuned plans vs plain per-batch launches "
+            "(host queries in, host results out)", "n_docs": docs.n, "impact": "f32", "query_nnz": UNEVEN_LAW,
+            "steps_per_point": 8, "results": rows, "wall_s": time.perf_counter() - t0}
 
 
 def run_uneven(args, w):
@@ -441,56 +581,94 @@ def run_uneven(args, w):
     gs.load()
     dev = torch.device("cuda:0")
     docs = synth.docs(w.n_docs, seed=0, threads=cores())
-    batches, ks = w.extra["batches"], w.extra["ks"]
     steps = max(3, min(args.steps, 8))
-    need = max(batches) * (steps + 2)
-    qs = synth.queries(need, seed=0, law=w.query_law)
     idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
                             torch.from_numpy(docs.weights).to(dev), docs.vocab, "f32")
-    max_nnz = max(int(qs.indptr[i + max(batches)] - qs.indptr[i]) for i in range(0, need - max(batches) + 1,
-                                                                                  max(batches)))
-    runner = gs.Runner(idx, max_batch=max(batches), max_q_nnz=max_nnz, max_k=max(ks))
-    results = []
-    for B in batches:
-        for k in ks:
-            subs = [qs.slice(i * B, (i + 1) * B) for i in range(steps + 1)]
-            host = [(torch.from_numpy(sb.indptr.astype(np.int32)).pin_memory(), torch.from_numpy(sb.terms).pin_memory(),
-                     torch.from_numpy(sb.weights).pin_memory()) for sb in subs]
-            # plain per-batch launches: default plan, no graph
-            opts = gs.make_opts("auto")
-            ws = gs.alloc_workspace(idx, B, max_nnz, k, opts, host_io=True)
-            hid = torch.empty((B, k), dtype=torch.int32).pin_memory()
-            hsc = torch.empty((B, k), dtype=torch.float32).pin_memory()
-            t_plain = []
-            for i, (a, b, c) in enumerate(host):
-                t = time.perf_counter()
-                gs.gs_search_host(idx, a, b, c, k, hid, hsc, ws, opts)
-                if i:
-                    t_plain.append((time.perf_counter() - t) * 1e3)
-            del ws
-            t_graph = []
-            for i, (a, b, c) in enumerate(host):
-                t = time.perf_counter()
-                runner.search(a, b, c, k, hid, hsc)
-                if i:  # the first call tunes and captures
-                    t_graph.append((time.perf_counter() - t) * 1e3)
-            row = {"batch": B, "k": k}
-            for name, ts in (("plain", t_plain), ("graph_tuned", t_graph)):
-                row[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
-                             "qps": B * len(ts) / (sum(ts) / 1e3)}
-            row["plan"] = runner.plan(B, k)
-            row["speedup"] = row["plain"]["p50_ms"] / row["graph_tuned"]["p50_ms"]
-            results.append(row)
-            print(json.dumps(row), file=sys.stderr, flush=True)
+    points = [(B, k) for B in w.extra["batches"] for k in w.extra["ks"]]
+    results = uneven_suite(gs, torch, idx, points, steps)
     return {"suite": "uneven", "metric": "p50/p99 batch latency and QPS, graph-replayed autotuned plans vs plain "
             "per-batch launches (host queries in, host results out)", "workload": w.name, "n_docs": w.n_docs,
-            "query_nnz": "70% Poisson(20), 25% Poisson(60), 5% uniform[150,300], clamped [1,300]",
-            "steps_per_point": steps, "results": results}
+            "query_nnz": UNEVEN_LAW, "steps_per_point": steps, "results": results}
+
+
+def serve_rates(gs, server, idx, rates, seconds, qs, rng, max_requests=20_000):
+    """Poisson arrivals at each offered rate; per-request latency from submit to completion."""
+    import threading
+    out = []
+    qi = 0
+    for rate in rates:
+        n = int(min(rate * seconds, max_requests))
+        gaps = rng.exponential(1.0 / rate, n)
+        ks = rng.choice([10, 100, 1000], n)
+        which = rng.integers(0, len(idx), n)
+        rows = [qs.row((qi + i) % qs.n) for i in range(n)]
+        qi += n
+        rows = [(np.ascontiguousarray(t), np.ascontiguousarray(wt)) for t, wt in rows]
+        tickets = [None] * n
+        lat = np.zeros(n)
+
+        def waiter():
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                lat[i] = server.wait(tickets[i], int(ks[i]), idx[which[i]].score_dtype, timeout_us=60_000_000)[2]
+
+        th = threading.Thread(target=waiter)
+        st0 = server.stats()
+        th.start()
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n):
+            due += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 0.002:
+                    time.sleep(due - now - 0.001)
+            tickets[i] = server.submit(int(which[i]), rows[i][0], rows[i][1], int(ks[i]))
+        th.join()
+        elapsed = time.perf_counter() - t0
+        st1 = server.stats()
+        nb = st1["batches"] - st0["batches"]
+        out.append({"offered_qps": rate, "requests": n, "sustained_qps": n / elapsed,
+                    "p50_ms": float(np.percentile(lat, 50) / 1e3), "p99_ms": float(np.percentile(lat, 99) / 1e3),
+                    "batches": nb, "mean_batch": (st1["batched_queries"] - st0["batched_queries"]) / max(nb, 1)})
+        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    return out
+
+
+SERVER_CFG = {"lanes": 4, "max_batch": 256, "max_q_nnz": 256 * 64, "max_k": 1000, "max_wait_us": 500}
+
+
+def serving_leg(gs, torch, dev, docs, d_indptr, d_terms, d_w, indexes, forms_out):
+    """Bounded leg of the default run: continuous batching over two resident FP16
+    indexes (1M documents and the headline's 8.84M), Poisson arrivals at two rates,
+    against the plain FP32 batch-500 form timed above."""
+    t0 = time.perf_counter()
+    big = indexes.get("f16") or gs.gs_index_build(d_indptr, d_terms, d_w, docs.vocab, "f16")
+    small_docs = synth.docs(1_000_000, seed=1, threads=cores())
+    small = gs.gs_index_build(torch.from_numpy(small_docs.indptr).to(dev), torch.from_numpy(small_docs.terms).to(dev),
+                              torch.from_numpy(small_docs.weights).to(dev), small_docs.vocab, "f16")
+    idx = [small, big]
+    server = gs.Server(idx, **SERVER_CFG)
+    qs = synth.queries(40_000, seed=9, law=synth.MIXTURE_LAW)
+    pts = serve_rates(gs, server, idx, (2000, 10000), 2.0, qs, np.random.default_rng(0))
+    stats = server.stats()
+    server.close()
+    small.free()
+    plain = forms_out.get("f32:term_parallel")
+    return {"metric": "per-request p50/p99 latency (submit to completion) and sustained QPS, Poisson arrivals, "
+            "continuous batching", "indexes": ["1M docs f16", f"{docs.n} docs f16"], "k": "uniform over {10,100,1000}",
+            "target_index": "uniform over the two", "query_nnz": UNEVEN_LAW,
+            "server": dict(SERVER_CFG, lanes_created=stats["lanes"], max_in_flight=stats["max_in_flight"]),
+            "plain_fp32_batch500": ({"qps": plain["qps"], "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"]}
+                                    if plain else None),
+            "results": pts, "wall_s": time.perf_counter() - t0}
 
 
 def run_serving(args, w):
     """Poisson arrivals over two resident FP16 indexes (1M and 8.84M docs), continuous batching."""
-    import threading
     import torch
     from paper_2606_26441_gb300 import gpusparse as gs
     gs.load()
@@ -519,59 +697,15 @@ def run_serving(args, w):
              "qps": 500 / (np.median(ts) / 1e3)}
     del ws, f32
     torch.cuda.empty_cache()
-    server = gs.Server(idx, lanes=4, max_batch=256, max_q_nnz=256 * 64, max_k=1000, max_wait_us=500)
-    rng = np.random.default_rng(0)
+    server = gs.Server(idx, **SERVER_CFG)
     qs = synth.queries(60_000, seed=9, law=w.query_law)
-    out = []
-    qi = 0
-    for rate in w.extra["rates"]:
-        n = int(min(rate * w.extra["seconds"], 20_000))
-        gaps = rng.exponential(1.0 / rate, n)
-        ks = rng.choice([10, 100, 1000], n)
-        which = rng.integers(0, 2, n)
-        rows = [qs.row((qi + i) % qs.n) for i in range(n)]
-        qi += n
-        rows = [(np.ascontiguousarray(t), np.ascontiguousarray(wt)) for t, wt in rows]
-        tickets = [None] * n
-        lat = np.zeros(n)
-        done = threading.Event()
-
-        def waiter():
-            for i in range(n):
-                while tickets[i] is None:
-                    time.sleep(0.0001)
-                lat[i] = server.wait(tickets[i], int(ks[i]), idx[which[i]].score_dtype, timeout_us=60_000_000)[2]
-            done.set()
-
-        th = threading.Thread(target=waiter)
-        st0 = server.stats()
-        th.start()
-        t0 = time.perf_counter()
-        due = t0
-        for i in range(n):
-            due += gaps[i]
-            while True:
-                now = time.perf_counter()
-                if now >= due:
-                    break
-                if due - now > 0.002:
-                    time.sleep(due - now - 0.001)
-            tickets[i] = server.submit(int(which[i]), rows[i][0], rows[i][1], int(ks[i]))
-        th.join()
-        elapsed = time.perf_counter() - t0
-        st1 = server.stats()
-        nb = st1["batches"] - st0["batches"]
-        out.append({"offered_qps": rate, "requests": n, "sustained_qps": n / elapsed,
-                    "p50_ms": float(np.percentile(lat, 50) / 1e3), "p99_ms": float(np.percentile(lat, 99) / 1e3),
-                    "batches": nb, "mean_batch": (st1["batched_queries"] - st0["batched_queries"]) / max(nb, 1)})
-        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    out = serve_rates(gs, server, idx, w.extra["rates"], w.extra["seconds"], qs, np.random.default_rng(0))
     stats = server.stats()
     server.close()
     return {"suite": "serving", "metric": "per-request p50/p99 latency (submit to completion) and sustained QPS "
             "under Poisson arrivals, continuous batching over two resident FP16 indexes",
             "indexes": ["1M docs f16", "8.84M docs f16"], "k": "uniform over {10,100,1000}",
-            "query_nnz": "mixture law", "server": {"lanes": stats["lanes"], "max_batch": 256,
-                                                   "max_wait_us": 500, "max_in_flight": stats["max_in_flight"]},
+            "query_nnz": "mixture law", "server": dict(SERVER_CFG, max_in_flight=stats["max_in_flight"]),
             "plain_fp32_batch500": plain, "results": out}
 
 
@@ -611,8 +745,37 @@ def run_sweep(args, w):
             "n_docs": w.n_docs, "batch": w.batch, "k": w.k, "results": out}
 
 
+def run_microbench():
+    """Builds paper_2606_26441_gb300/microbench/rates.cu (nvcc, sm_103a) and prints its rates as the
+    '- name: value' lines that microbench_rates() reads."""
+    src = os.path.join(ROOT, "paper_2606_26441_gb300", "microbench", "rates.cu")
+    exe = os.path.join(tempfile.mkdtemp(), "rates")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
+                   check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    print(out, end="")
+    names = {"red.shared.add.s32 distinct banks": "red.shared.add.s32 distinct banks, lanes per clk per SM",
+             "red.shared.add.s32 random cells": "red.shared.add.s32 random cells, lanes per clk per SM",
+             "red.shared.add.f32 distinct banks": "red.shared.add.f32 distinct banks, lanes per clk per SM",
+             "red.shared.add.f32 random cells": "red.shared.add.f32 random cells, lanes per clk per SM",
+             "red.shared.add.u64 distinct": "red.shared.add.u64 distinct banks, lanes per clk per SM",
+             "red.shared.add.u64 random cells": "red.shared.add.u64 random cells, lanes per clk per SM"}
+    for line in out.splitlines():
+        for pre, key in names.items():
+            if line.startswith(pre + " "):
+                print(f"- {key}: {float(line.split('lanes/s')[1].split()[0]):.2f}")
+        if line.startswith("ffma"):
+            print(f"- ffma, FMA lanes per clk per SM: {float(line.split('TFLOP/s')[1].split()[0]):.2f}")
+            print(f"- ffma, TFLOP/s: {float(line.split('ms')[1].split()[0]):.2f}")
+        if line.startswith("red.global.add.f32"):
+            print(f"- red.global.add.f32 random cells (L2), G per s: {float(line.split('ms')[1].split()[0]):.1f}")
+
+
 def main():
     args = parse()
+    if args.microbench:
+        run_microbench()
+        return
     world, rank, local = dist_setup(args)
     w = synth.WORKLOADS[args.workload]
     if w.extra.get("batches"):

@@ -209,10 +209,10 @@ gs_status dp_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   record_stage(opts, 4, s);
   if (ix->impact == GS_IMPACT_U8)
     topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.rows), p.ld, ix->N,
-                                                              k, out_ids, static_cast<int32_t*>(out_scores));
+                                                              k, out_ids, static_cast<int32_t*>(out_scores), nullptr);
   else
     topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const float*>(p.rows), p.ld, ix->N, k,
-                                                            out_ids, static_cast<float*>(out_scores));
+                                                            out_ids, static_cast<float*>(out_scores), nullptr);
   GS_LAUNCH_CHECK();
   record_stage(opts, 5, s);
   return GS_OK;

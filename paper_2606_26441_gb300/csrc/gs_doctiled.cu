@@ -1149,9 +1149,9 @@ struct DtOverflow {
   uint32_t* q_over;   // [B]
   uint32_t* g_mark;   // [ng]
   uint32_t* n_groups;
-  int32_t* groups;    // [ng]
-  uint32_t* hist;     // [B][2048]
-  uint32_t* tiebm;    // [B][bm_words]
+  int32_t* groups;    // [ng]; NULL: no recovery list (dense rows)
+  uint32_t* hist;     // [B][2048]; NULL: nothing to clear
+  uint32_t* tiebm;    // [B][bm_words]; NULL: nothing to clear
   int G;
 };
 
@@ -1185,10 +1185,12 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
       ov.q_over[q] = 1u;
       cand_cnt[q] = 0u;
       const int g = q / ov.G;
-      if (atomicExch(ov.g_mark + g, 1u) == 0u) ov.groups[atomicAdd(ov.n_groups, 1u)] = g;
+      if (ov.groups && atomicExch(ov.g_mark + g, 1u) == 0u) ov.groups[atomicAdd(ov.n_groups, 1u)] = g;
     }
-    for (int i = threadIdx.x; i < 2048; i += blockDim.x) ov.hist[(int64_t)q * 2048 + i] = 0u;
-    for (int64_t w = threadIdx.x; w < bm_words; w += blockDim.x) ov.tiebm[(int64_t)q * bm_words + w] = 0u;
+    if (ov.hist)
+      for (int i = threadIdx.x; i < 2048; i += blockDim.x) ov.hist[(int64_t)q * 2048 + i] = 0u;
+    if (ov.tiebm)
+      for (int64_t w = threadIdx.x; w < bm_words; w += blockDim.x) ov.tiebm[(int64_t)q * bm_words + w] = 0u;
     return;
   }
   const int64_t n = min((int64_t)raw, cap);
@@ -1444,6 +1446,212 @@ gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32
   if (c.HK == kHeadTensor) return launch_tiles_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
   return launch_tiles_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
 }
+
+// ---- exact top-k of dense score rows ------------------------------------
+//
+// Rows written densely (the term-parallel and doc-parallel paths) get the same
+// sampled-threshold selection as the doc-tiled path: the k-th largest score of
+// every R-th chunk of kDenseChunk documents bounds the row's k-th score from
+// below; one pass over the row keeps the documents above that bound
+// (candidates) and marks those equal to it (ties); the final kernel selects the
+// top k of the candidates.  A row whose candidates overflow their list is
+// selected again by the radix select over the whole row.
+
+constexpr int kDenseChunk = 1024;
+
+struct DenseConfig {
+  int R = 0;  // 0: no sample, the radix select over whole rows
+  int n_sample = 0;
+  int64_t sample_docs = 0, cap = 0, bm_words = 0;
+};
+
+DenseConfig dense_config(const gs_index* ix, int k) {
+  DenseConfig c;
+  const int nt_full = (int)(ix->N / kDenseChunk);
+  int R = kDefaultSampleStride;
+  while (R > 1 && (int64_t)((nt_full + R - 1) / R) * kDenseChunk < 2 * (int64_t)k) R /= 2;
+  if (R <= 1 || (int64_t)((nt_full + R - 1) / R) * kDenseChunk < (int64_t)k) R = 0;
+  c.R = R;
+  if (R == 0) return c;
+  c.n_sample = (nt_full + R - 1) / R;
+  c.sample_docs = (int64_t)c.n_sample * kDenseChunk;
+  const int64_t n_round = (ix->N + 255) / 256 * 256;
+  c.cap = std::min<int64_t>(n_round, (4 * (int64_t)k * R + 4096 + 255) / 256 * 256);
+  c.bm_words = (ix->N + 31) / 32;
+  return c;
+}
+
+struct DensePlan {
+  uint32_t* samp;     // [B][sample_docs]
+  uint32_t* theta;    // [B]
+  uint2* cand;        // [B][cap]
+  uint32_t* cand_cnt; // [B]; cleared block [B cand_cnt][B q_over][B g_mark][n_groups]
+  uint32_t* q_over;
+  uint32_t* g_mark;
+  uint32_t* n_groups;
+  uint32_t* tiebm;    // [B][bm_words]
+  size_t zero_bytes;
+};
+
+DensePlan carve_dense(void* ws, int B, const DenseConfig& c, size_t* bytes) {
+  Carver cv(ws);
+  DensePlan p{};
+  p.samp = cv.take<uint32_t>((size_t)B * std::max<int64_t>(c.sample_docs, 1));
+  p.theta = cv.take<uint32_t>(B);
+  p.cand = cv.take<uint2>((size_t)B * std::max<int64_t>(c.cap, 1));
+  p.zero_bytes = sizeof(uint32_t) * (3 * (size_t)B + 1);
+  p.cand_cnt = cv.take<uint32_t>(3 * (size_t)B + 1);
+  p.q_over = p.cand_cnt ? p.cand_cnt + B : nullptr;
+  p.g_mark = p.cand_cnt ? p.q_over + B : nullptr;
+  p.n_groups = p.cand_cnt ? p.g_mark + B : nullptr;
+  p.tiebm = cv.take<uint32_t>((size_t)B * std::max<int64_t>(c.bm_words, 1));
+  *bytes = cv.size();
+  return p;
+}
+
+// chunk j R of every row -> sample row (one thread per 16 bytes)
+__global__ void dense_sample_gather_kernel(const uint4* __restrict__ rows, int64_t ld4, int R,
+                                           uint4* __restrict__ samp, int64_t sample4) {
+  const int q = blockIdx.y;
+  const int j = blockIdx.x;  // sample chunk
+  constexpr int kChunk4 = kDenseChunk / 4;
+  for (int i = threadIdx.x; i < kChunk4; i += blockDim.x)
+    samp[(int64_t)q * sample4 + (int64_t)j * kChunk4 + i] = rows[(int64_t)q * ld4 + (int64_t)j * R * kChunk4 + i];
+}
+
+// One pass over the rows: documents above theta_q become candidates (one
+// warp-wide slot reservation per 128 documents), documents equal to it set
+// their bit in the tie bitmap.  Lane l of a warp step holds documents
+// 4 l .. 4 l + 3 of the step (one 16-byte load).
+template <typename ST>
+__global__ void __launch_bounds__(256) dense_emit_kernel(const ST* __restrict__ rows, int64_t ld, int64_t N,
+                                                         const uint32_t* __restrict__ theta_bits, int R,
+                                                         uint2* __restrict__ cand, uint32_t* __restrict__ cand_cnt,
+                                                         int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words) {
+  const int q = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const uint32_t th = theta_key<ST>(theta_bits, q, R);
+  const ST* row = rows + (int64_t)q * ld;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t d0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 128; d0 < N;
+       d0 += warps * 128) {
+    const int64_t d = d0 + 4 * lane;
+    uint32_t gt = 0, eq = 0;
+    uint32_t key[4] = {0, 0, 0, 0};
+    if (d < N) {  // ld is a multiple of 32: the 16 bytes lie inside the row
+      const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(row + d));
+      const uint32_t rv[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ST v;
+        memcpy(&v, &rv[i], 4);
+        key[i] = score_key(v);
+        const bool in = d + i < N;
+        gt |= (uint32_t)(in && key[i] > th) << i;
+        eq |= (uint32_t)(in && key[i] == th) << i;
+      }
+    }
+    const int n = __popc(gt);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tot > 0) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&cand_cnt[q], (uint32_t)tot);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      uint32_t slot = base + (uint32_t)(incl - n);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if ((gt >> i) & 1u) {
+          if (slot < cap) cand[(int64_t)q * cap + slot] = make_uint2(key[i], (uint32_t)(d + i));
+          ++slot;
+        }
+    }
+    // tie words: 32 documents = 8 lanes x 4 bits
+    uint32_t word = eq << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    if ((lane & 7) == 0 && word) tiebm[(int64_t)q * bm_words + ((d0 >> 5) + (lane >> 3))] = word;
+  }
+}
+
+}  // namespace
+
+gs_status dense_topk_workspace_bytes(const gs_index* ix, int32_t B, int32_t k, size_t* bytes) {
+  const DenseConfig c = dense_config(ix, k);
+  if (c.R == 0) {
+    *bytes = 0;
+    return GS_OK;
+  }
+  carve_dense(nullptr, B, c, bytes);
+  return GS_OK;
+}
+
+gs_status dense_topk(const gs_index* ix, const void* rows, int64_t ld, int32_t B, int32_t k, int32_t* out_ids,
+                     void* out_scores, void* ws, size_t ws_bytes, uint32_t* flags, cudaStream_t s) {
+  const bool is_int = ix->impact == GS_IMPACT_U8;
+  const DenseConfig c = dense_config(ix, k);
+  if (c.R == 0 || (ld & 31) != 0) {
+    if (is_int)
+      topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(static_cast<const int32_t*>(rows), ld, ix->N, k,
+                                                                out_ids, static_cast<int32_t*>(out_scores), nullptr);
+    else
+      topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(static_cast<const float*>(rows), ld, ix->N, k,
+                                                              out_ids, static_cast<float*>(out_scores), nullptr);
+    GS_LAUNCH_CHECK();
+    return GS_OK;
+  }
+  size_t need = 0;
+  DensePlan p = carve_dense(ws, B, c, &need);
+  if (need > ws_bytes) return GS_ERR_WORKSPACE;
+  GS_CUDA_TRY(cudaMemsetAsync(p.cand_cnt, 0, p.zero_bytes, s));
+  GS_CUDA_TRY(cudaMemsetAsync(p.tiebm, 0, sizeof(uint32_t) * (size_t)B * c.bm_words, s));
+  dense_sample_gather_kernel<<<dim3((unsigned)c.n_sample, (unsigned)B), 256, 0, s>>>(
+      static_cast<const uint4*>(rows), ld / 4, c.R, reinterpret_cast<uint4*>(p.samp), c.sample_docs / 4);
+  GS_LAUNCH_CHECK();
+  const int sms = ix->sms > 0 ? ix->sms : 1;
+  // about 16 resident warps per SM for the whole batch
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ix->N + 1023) / 1024,
+                                                                       (int64_t)sms * 16 / std::max(B, 1) + 1));
+  const DtOverflow ov{p.q_over, p.g_mark, p.n_groups, nullptr, nullptr, nullptr, 1};
+  if (is_int) {
+    kth_score_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const int32_t*>(p.samp), c.sample_docs,
+                                                             c.sample_docs, k, p.theta);
+    GS_LAUNCH_CHECK();
+    dense_emit_kernel<int32_t><<<dim3(gx, (unsigned)B), 256, 0, s>>>(static_cast<const int32_t*>(rows), ld, ix->N,
+                                                                     p.theta, c.R, p.cand, p.cand_cnt, c.cap, p.tiebm,
+                                                                     c.bm_words);
+    GS_LAUNCH_CHECK();
+    dt_final_kernel<int32_t, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
+                                                       p.theta, c.R, k, out_ids, static_cast<int32_t*>(out_scores),
+                                                       flags, ov);
+    GS_LAUNCH_CHECK();
+    topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(static_cast<const int32_t*>(rows), ld, ix->N, k,
+                                                              out_ids, static_cast<int32_t*>(out_scores), p.q_over);
+  } else {
+    kth_score_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(reinterpret_cast<const float*>(p.samp), c.sample_docs,
+                                                           c.sample_docs, k, p.theta);
+    GS_LAUNCH_CHECK();
+    dense_emit_kernel<float><<<dim3(gx, (unsigned)B), 256, 0, s>>>(static_cast<const float*>(rows), ld, ix->N,
+                                                                   p.theta, c.R, p.cand, p.cand_cnt, c.cap, p.tiebm,
+                                                                   c.bm_words);
+    GS_LAUNCH_CHECK();
+    dt_final_kernel<float, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
+                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov);
+    GS_LAUNCH_CHECK();
+    topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(static_cast<const float*>(rows), ld, ix->N, k,
+                                                            out_ids, static_cast<float*>(out_scores), p.q_over);
+  }
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+namespace {
 
 }  // namespace
 

@@ -17,4 +17,12 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
                     int32_t B, int64_t q_nnz, int32_t k, int32_t* out_ids, void* out_scores, void* ws,
                     size_t ws_bytes, uint32_t* flags, const gs_search_opts* opts, cudaStream_t s);
 
+// Exact top-k of B dense score rows (row q at rows + q * ld, N scores, float
+// or int32 on the uint8 path) by a sampled threshold and one candidate pass;
+// rows whose candidates overflow are selected again over the whole row.  The
+// workspace is separate from the rows; flags: a flag word.
+gs_status dense_topk_workspace_bytes(const gs_index* ix, int32_t B, int32_t k, size_t* bytes);
+gs_status dense_topk(const gs_index* ix, const void* rows, int64_t ld, int32_t B, int32_t k, int32_t* out_ids,
+                     void* out_scores, void* ws, size_t ws_bytes, uint32_t* flags, cudaStream_t s);
+
 }  // namespace gs

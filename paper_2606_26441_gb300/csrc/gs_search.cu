@@ -138,34 +138,57 @@ __global__ void zero_kernel(uint32_t* __restrict__ p, int64_t words) {
   for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) p[i] = 0u;
 }
 
-__device__ __forceinline__ int4 ldg_nc_v4(const void* p) {
+// Posting loads are streamed with an L2 evict-first policy, so that the
+// score rows the reductions update keep their L2 lines.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int4 ldg_stream_v4(const void* p, uint64_t pol) {
   int4 v;
-  asm volatile("ld.global.nc.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ldg_stream_v2(const void* p, uint64_t pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldg_stream_u32(const void* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
 
 // four impacts of one lane (postings 4j..4j+3 of a block), as float (or int)
 template <int IMPACT>
-__device__ __forceinline__ void load4_impacts(const uint8_t* blk, int j, float (&x)[4], int (&xi)[4]) {
+__device__ __forceinline__ void load4_impacts(const uint8_t* blk, int j, float (&x)[4], int (&xi)[4], uint64_t pol) {
   if (IMPACT == GS_IMPACT_F32) {
-    int4 v = ldg_nc_v4(blk + 128 + j * 16);
+    int4 v = ldg_stream_v4(blk + 128 + j * 16, pol);
     x[0] = __int_as_float(v.x); x[1] = __int_as_float(v.y); x[2] = __int_as_float(v.z); x[3] = __int_as_float(v.w);
   } else if (IMPACT == GS_IMPACT_F16) {
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(blk + 128 + j * 8));
+    uint2 v = ldg_stream_v2(blk + 128 + j * 8, pol);
     __half2 a = *reinterpret_cast<__half2*>(&v.x), b = *reinterpret_cast<__half2*>(&v.y);
     float2 fa = __half22float2(a), fb = __half22float2(b);
     x[0] = fa.x; x[1] = fa.y; x[2] = fb.x; x[3] = fb.y;
   } else if (IMPACT == GS_IMPACT_BF16) {
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(blk + 128 + j * 8));
+    uint2 v = ldg_stream_v2(blk + 128 + j * 8, pol);
     __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&v.x), b = *reinterpret_cast<__nv_bfloat162*>(&v.y);
     float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     x[0] = fa.x; x[1] = fa.y; x[2] = fb.x; x[3] = fb.y;
   } else {
-    uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(blk + 128 + j * 4));
+    uint32_t v = ldg_stream_u32(blk + 128 + j * 4, pol);
     xi[0] = v & 0xff; xi[1] = (v >> 8) & 0xff; xi[2] = (v >> 16) & 0xff; xi[3] = v >> 24;
   }
 }
 
+// Each warp walks a work item 4 blocks per step (8 lanes per block, 4
+// postings per lane, 128-bit loads).  kUnroll steps are loaded before any of
+// their postings is added: 4 steps measured no faster than 1 (the kernel is
+// bound by the L2 reduction rate) and halve the resident warps, so 1.
 template <int IMPACT>
 __global__ void __launch_bounds__(256) tp_scatter_kernel(
     const uint8_t* __restrict__ blocks, const int64_t* __restrict__ term_block, const int32_t* __restrict__ pair_q,
@@ -173,7 +196,10 @@ __global__ void __launch_bounds__(256) tp_scatter_kernel(
     const int64_t* __restrict__ pair_chunk, int64_t npairs, const Header* __restrict__ hdr, int chunk_blocks,
     int64_t ld, void* __restrict__ rows) {
   constexpr int bb = block_bytes(IMPACT);
+  constexpr int kUnroll = 1;
+  const uint64_t pol = evict_first_policy();
   const int lane = threadIdx.x & 31;
+  const int j = lane & 7;
   const int64_t total = hdr->total_chunks;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
@@ -183,34 +209,33 @@ __global__ void __launch_bounds__(256) tp_scatter_kernel(
     const int64_t b_end = term_block[t + 1];
     const int64_t b0 = term_block[t] + (c - pair_chunk[p]) * chunk_blocks;
     const int64_t b1 = min(b0 + chunk_blocks, b_end);
-    const int j = lane & 7;
-    if (IMPACT == GS_IMPACT_U8) {
-      int32_t* row = static_cast<int32_t*>(rows) + (int64_t)q * ld;
-      const int32_t w = pair_wi[p];
-      for (int64_t b = b0 + (lane >> 3); b < b1; b += 4) {
-        const uint8_t* blk = blocks + b * bb;
-        const int4 ids = ldg_nc_v4(blk + j * 16);
-        float x[4];
-        int xi[4];
-        load4_impacts<IMPACT>(blk, j, x, xi);
-        if (ids.x >= 0) atomicAdd(row + ids.x, w * xi[0]);
-        if (ids.y >= 0) atomicAdd(row + ids.y, w * xi[1]);
-        if (ids.z >= 0) atomicAdd(row + ids.z, w * xi[2]);
-        if (ids.w >= 0) atomicAdd(row + ids.w, w * xi[3]);
+    const float wf = pair_wf[p];
+    const int32_t wi = pair_wi[p];
+    float* rowf = static_cast<float*>(rows) + (int64_t)q * ld;
+    int32_t* rowi = static_cast<int32_t*>(rows) + (int64_t)q * ld;
+    for (int64_t b = b0 + (lane >> 3); b < b1; b += 4 * kUnroll) {
+      int4 ids[kUnroll];
+      float x[kUnroll][4];
+      int xi[kUnroll][4];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        ids[u] = make_int4(-1, -1, -1, -1);
+        const int64_t bu = b + 4 * u;
+        if (bu < b1) {
+          const uint8_t* blk = blocks + bu * bb;
+          ids[u] = ldg_stream_v4(blk + j * 16, pol);
+          load4_impacts<IMPACT>(blk, j, x[u], xi[u], pol);
+        }
       }
-    } else {
-      float* row = static_cast<float*>(rows) + (int64_t)q * ld;
-      const float w = pair_wf[p];
-      for (int64_t b = b0 + (lane >> 3); b < b1; b += 4) {
-        const uint8_t* blk = blocks + b * bb;
-        const int4 ids = ldg_nc_v4(blk + j * 16);
-        float x[4];
-        int xi[4];
-        load4_impacts<IMPACT>(blk, j, x, xi);
-        if (ids.x >= 0) atomicAdd(row + ids.x, w * x[0]);
-        if (ids.y >= 0) atomicAdd(row + ids.y, w * x[1]);
-        if (ids.z >= 0) atomicAdd(row + ids.z, w * x[2]);
-        if (ids.w >= 0) atomicAdd(row + ids.w, w * x[3]);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int id[4] = {ids[u].x, ids[u].y, ids[u].z, ids[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (id[e] < 0) continue;  // padding (and steps past the item)
+          if (IMPACT == GS_IMPACT_U8) atomicAdd(rowi + id[e], wi * xi[u][e]);
+          else atomicAdd(rowf + id[e], wf * x[u][e]);
+        }
       }
     }
   }
@@ -225,10 +250,13 @@ struct TpPlan {
   int64_t* pair_chunk;
   void* rows;  // [B x ld]
   int64_t ld;
+  void* topk_ws;  // the dense-row top-k's workspace
+  size_t topk_bytes;
 };
 
 // Workspace = [term-parallel region (header first)][doc-tiled region][host-io region]
-TpPlan carve_tp(void* ws, const gs_index* ix, int32_t B, int64_t q_nnz, bool with_rows, size_t* bytes) {
+TpPlan carve_tp(void* ws, const gs_index* ix, int32_t B, int64_t q_nnz, bool with_rows, size_t* bytes,
+                int32_t k = 1) {
   Carver c(ws);
   TpPlan p{};
   p.hdr = c.take<Header>(1);
@@ -239,6 +267,9 @@ TpPlan carve_tp(void* ws, const gs_index* ix, int32_t B, int64_t q_nnz, bool wit
   p.pair_chunk = c.take<int64_t>(q_nnz + 1);
   p.ld = (ix->N + 31) / 32 * 32;
   p.rows = with_rows ? (void*)c.take<uint32_t>((size_t)B * p.ld) : nullptr;
+  p.topk_bytes = 0;
+  if (with_rows) dense_topk_workspace_bytes(ix, B, k, &p.topk_bytes);
+  p.topk_ws = p.topk_bytes ? (void*)c.take<uint8_t>(p.topk_bytes) : nullptr;
   *bytes = c.size();
   return p;
 }
@@ -297,16 +328,9 @@ gs_status run_tp_scores(const gs_index* ix, const int32_t* q_indptr, const int32
   return GS_OK;
 }
 
-gs_status run_topk_dense(const gs_index* ix, const void* rows, int64_t ld, int32_t B, int32_t k, int32_t* out_ids,
+gs_status run_topk_dense(const gs_index* ix, const TpPlan& p, int32_t B, int32_t k, int32_t* out_ids,
                          void* out_scores, cudaStream_t s) {
-  if (ix->impact == GS_IMPACT_U8)
-    topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(static_cast<const int32_t*>(rows), ld, ix->N, k,
-                                                              out_ids, static_cast<int32_t*>(out_scores));
-  else
-    topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(static_cast<const float*>(rows), ld, ix->N, k,
-                                                            out_ids, static_cast<float*>(out_scores));
-  GS_LAUNCH_CHECK();
-  return GS_OK;
+  return dense_topk(ix, p.rows, p.ld, B, k, out_ids, out_scores, p.topk_ws, p.topk_bytes, &p.hdr->flags, s);
 }
 
 int resolve_algo(const gs_index* ix, const gs_search_opts* opts) {
@@ -336,7 +360,7 @@ extern "C" gs_status gs_search_workspace_size(const gs_index* ix, int32_t B, int
   if (st != GS_OK) return st;
   const int algo = resolve_algo(ix, opts);
   size_t tp_bytes = 0;
-  carve_tp(nullptr, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes);
+  carve_tp(nullptr, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes, std::max(k, 1));
   if (algo == GS_ALGO_DOC_PARALLEL) {
     size_t dp = 0;
     st = dp_workspace_bytes(ix, B, &dp);
@@ -374,7 +398,7 @@ extern "C" gs_status gs_search(const gs_index* ix, const int32_t* q_indptr, cons
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int algo = resolve_algo(ix, opts);
   size_t tp_bytes = 0;
-  TpPlan p = carve_tp(workspace, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes);
+  TpPlan p = carve_tp(workspace, ix, B, q_nnz, algo == GS_ALGO_TERM_PARALLEL, &tp_bytes, k);
   GS_CUDA_TRY(cudaMemsetAsync(p.hdr, 0, sizeof(Header), s));
   if (algo == GS_ALGO_DOC_PARALLEL) {
     return dp_search(ix, q_indptr, q_terms, q_w, B, q_nnz, k, out_ids, out_scores,
@@ -388,7 +412,7 @@ extern "C" gs_status gs_search(const gs_index* ix, const int32_t* q_indptr, cons
   const int chunk = (opts && opts->chunk_blocks > 0) ? opts->chunk_blocks : kDefaultChunkBlocks;
   st = run_tp_scores(ix, q_indptr, q_terms, q_w, B, q_nnz, p, chunk, p.rows, p.ld, opts, s);
   if (st != GS_OK) return st;
-  st = run_topk_dense(ix, p.rows, p.ld, B, k, out_ids, out_scores, s);
+  st = run_topk_dense(ix, p, B, k, out_ids, out_scores, s);
   record_stage(opts, 5, s);
   return st;
 }

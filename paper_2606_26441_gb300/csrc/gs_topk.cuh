@@ -227,11 +227,13 @@ __device__ __forceinline__ uint32_t radix_kth_key(const ST* __restrict__ r, int6
 
 // Top-k of `rows` dense rows: row r is S[r * ld .. r * ld + N).  Scores are
 // float (float paths) or int32 (uint8 path).  Output row-major [rows x k].
+// only: NULL, or [rows] flags: rows whose flag is 0 are skipped.
 template <typename ST>
 __global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST* __restrict__ S, int64_t ld,
                                                                        int64_t N, int k,
                                                                        int32_t* __restrict__ out_ids,
-                                                                       ST* __restrict__ out_scores) {
+                                                                       ST* __restrict__ out_scores,
+                                                                       const uint32_t* __restrict__ only) {
   // the histograms and, after the radix passes, the k candidates share storage
   __shared__ uint32_t smem_raw[kHistCopies * 2048];
   static_assert(2 * GS_MAX_K <= kHistCopies * 2048, "candidates must fit in the histogram storage");
@@ -244,6 +246,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_dense_rows_kernel(const ST*
   __shared__ int s_gt;
 
   const int row = blockIdx.x;
+  if (only && __ldcg(only + row) == 0u) return;
   const ST* __restrict__ r = S + (int64_t)row * ld;
 
   int need = k;

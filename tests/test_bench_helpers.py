@@ -73,3 +73,36 @@ def test_byte_counts_against_direct_counts():
         a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + 8)])
         want += int(sum(main_df[t] for t in set(qs.terms[a:e].tolist())))
     assert extra["postings"] == want and got == want * (4 + 1)
+
+
+def test_compute_work_against_direct_counts():
+    """Tail reductions = (query, posting) pairs of non-head terms outside the sample
+    tiles; head FLOPs = 2 x 16 queries x the group's distinct head terms x main documents."""
+    docs = synth.docs(3_000, seed=12)
+    qs = synth.queries(20, seed=12)
+    df = np.bincount(docs.terms, minlength=docs.vocab).astype(np.int64)
+    T, R, ns, H, G = 256, 4, 2, 5, 8
+    sdf = bench.sample_term_counts(docs, T, R, ns)
+    plan = types.SimpleNamespace(group_queries=G, sample_tiles=ns, tile_docs=T)
+    tail, head_flops = bench.compute_work(plan, docs, qs, df, sdf, H)
+    head = sorted(range(docs.vocab), key=lambda t: (-df[t], t))[:H]
+    want_tail, rows = 0, 0
+    for g0 in range(0, qs.n, G):
+        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
+        for t in qs.terms[a:e].tolist():
+            if t not in head:
+                want_tail += int(df[t] - sdf[t])
+        rows += len({t for t in qs.terms[a:e].tolist() if t in head})
+    assert tail == want_tail
+    assert head_flops == 2 * 16 * rows * (docs.n - ns * T)
+
+
+def test_microbench_rates_parse(tmp_path, monkeypatch):
+    f = tmp_path / "mb.md"
+    f.write_text("# probe\n\n- red.shared.add.s32 random cells, lanes per clk per SM: 12.5\n"
+                 "- ffma, FMA lanes per clk per SM: 127.9 (at 2070 MHz)\n- not a number: n/a\n")
+    monkeypatch.setattr(bench, "MICROBENCH_FILE", str(f))
+    r = bench.microbench_rates()
+    assert r["red.shared.add.s32 random cells, lanes per clk per SM"] == 12.5
+    assert r["ffma, FMA lanes per clk per SM"] == 127.9
+    assert "not a number" not in r
