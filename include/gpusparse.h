@@ -104,6 +104,9 @@ typedef enum {
                                    was recomputed exactly (radix select of
                                    its k-th score over fresh scores of every
                                    document), so the results stay exact */
+#define GS_FLAG_TIMEOUT 8u      /* a bounded device wait gave up (the
+                                   tensor-memory head waiting for its MMAs):
+                                   results of that call are undefined */
 #define GS_FLAG_BAD_INDPTR 16u  /* the query CSR row pointer was not monotone
                                    or ended past q_nnz: results undefined */
 
@@ -179,10 +182,13 @@ typedef struct {
                             sample (0 = auto, 1 = no sampling: every
                             document is a candidate) */
   int32_t use_head;      /* DOC_TILED dense head (requires 16 queries per
-                            group and an index with a head): 0 = auto (FMAs
-                            for FP32 impacts, tensor-core MMAs otherwise),
-                            1 = CUDA-core FMAs, 2 = tensor-core MMAs,
-                            -1 = off */
+                            group and an index with a head): 0 = auto
+                            (FMAs for FP32 impacts, warp-level tensor-core
+                            MMAs otherwise),
+                            1 = CUDA-core FMAs, 2 = warp-level tensor-core
+                            MMAs (mma.sync), 3 = tensor-memory MMAs (tcgen05,
+                            FP32 impacts and heads of at most 24 rows only,
+                            else GS_ERR_UNSUPPORTED), -1 = off */
   void* const* stage_events; /* NULL, or GS_NUM_STAGE_EVENTS cudaEvent_t */
 } gs_search_opts;
 

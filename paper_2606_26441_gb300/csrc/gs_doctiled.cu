@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "gs_doctiled.cuh"
+#include "gs_tc05.cuh"
 #include "gs_topk.cuh"
 
 namespace gs {
@@ -46,8 +47,12 @@ constexpr int kMaxGroup = 64;                // queries per group (thresholds ke
 constexpr int kHeadG = 16;                   // queries per group when the dense head is used
 constexpr int kDefaultGroup = 16;
 constexpr int kDefaultSampleStride = 64;
-// dense head kinds: none, CUDA-core FMAs, tensor-core MMAs
-enum { kHeadNone = 0, kHeadFma = 1, kHeadTensor = 2 };
+// dense head kinds: none, CUDA-core FMAs, tensor-core MMAs (warp-level
+// mma.sync), tensor-memory MMAs (tcgen05, FP32 impacts)
+enum { kHeadNone = 0, kHeadFma = 1, kHeadTensor = 2, kHeadTc05 = 3 };
+constexpr int kTc05MaxRows = 24;     // head rows the tensor-memory head takes (3 k-steps of 8)
+constexpr uint32_t kTc05Cols = 256;  // tensor-memory columns per CTA (two CTAs per SM)
+constexpr uint32_t kTc05WaitTries = 1u << 22;
 
 struct DtConfig {
   int G = 0, T = 0, m = 0, R = 0;  // R = 0: no sampling
@@ -66,16 +71,21 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   if (c->T % ix->tile_docs != 0 || (c->T & (c->T - 1)) != 0 || c->T > 8192) return GS_ERR_INVALID_ARG;
   c->m = c->T / ix->tile_docs;
   int G = (opts && opts->group_queries > 0) ? opts->group_queries : kDefaultGroup;
-  // the dense head serves groups of kHeadG queries: FMAs (use_head 1, and
-  // FP32 impacts by default) or tensor-core MMAs (use_head 2, and the other
-  // impacts by default); use_head < 0 turns it off
+  // the dense head serves groups of kHeadG queries: CUDA-core FMAs (use_head
+  // 1, and FP32 impacts by default), warp-level tensor-core MMAs (use_head 2,
+  // and the other impacts by default) or tensor-memory MMAs (use_head 3, FP32
+  // impacts, at most 24 head rows); use_head < 0 turns it off
   const int use_head = opts ? opts->use_head : 0;
-  if (use_head > 2) return GS_ERR_INVALID_ARG;
+  if (use_head > 3) return GS_ERR_INVALID_ARG;
   const bool head = ix->head_H > 0 && G == kHeadG && use_head >= 0;
+  // the tensor-memory head (use_head 3): FP32 impacts, at most 24 head rows
+  if (head && use_head == 3 && (ix->impact != GS_IMPACT_F32 || ix->head_H > kTc05MaxRows)) return GS_ERR_UNSUPPORTED;
   c->HK = !head ? kHeadNone
                 : (use_head == 1 ? kHeadFma
                                  : (use_head == 2 ? kHeadTensor
-                                                  : (ix->impact == GS_IMPACT_F32 ? kHeadFma : kHeadTensor)));
+                                                  : (use_head == 3 ? kHeadTc05
+                                                                   : (ix->impact == GS_IMPACT_F32 ? kHeadFma
+                                                                                                  : kHeadTensor))));
   c->H = head ? ix->head_H : 0;
   G = head ? kHeadG : std::min(std::min(G, B), kMaxGroup);
   if ((int64_t)G * c->T * 4 > kDtMaxAccBytes) {
@@ -367,6 +377,18 @@ __device__ __forceinline__ uint32_t impact_tf32(V v, int j) {
   }
 }
 
+// Barrier of the 4 warps of warpgroup wg (named barriers 1..4; immediate ids,
+// so that the kernel reserves 5 barriers rather than all 16, which would allow
+// only one resident CTA per SM).
+__device__ __forceinline__ void wg_barrier(int wg) {
+  switch (wg) {
+    case 0: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
+  }
+}
+
 // a score cell of the tail: the float itself, or a fixed-point integer times 2^-S
 __device__ __forceinline__ float tail_value(float v, bool fx, float isc) {
   return fx ? (float)__float_as_int(v) * isc : v;
@@ -394,7 +416,8 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
     uint32_t* __restrict__ cand_cnt, int64_t cap, uint32_t* __restrict__ tiebm, int64_t bm_words,
     const uint8_t* __restrict__ head_dense, int64_t head_ld, int H, const uint32_t* __restrict__ headw,
     const int32_t* __restrict__ head_act, const int32_t* __restrict__ head_nact, int tiles_per_cta, int n_tiles,
-    const int32_t* __restrict__ fixp, const int32_t* __restrict__ qscale, DtRecover rec) {
+    const int32_t* __restrict__ fixp, const int32_t* __restrict__ qscale, DtRecover rec,
+    uint32_t* __restrict__ flags) {
   using AccT = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   constexpr int bb = block_bytes(IMPACT);
   constexpr bool HEAD = HK != kHeadNone;
@@ -425,6 +448,10 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ uint4 s_af[HEAD ? (GS_MAX_HEAD_TERMS / 8) * 32 * 2 : 1];
   AccT* s_w = reinterpret_cast<AccT*>(s_af);
   __shared__ int s_tc;  // the head runs on the tensor cores
+  // tensor-memory head: the CTA's tensor-memory columns and one MMA-completion
+  // barrier per warpgroup (warpgroup w uses columns 64 w .. 64 w + 63)
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar[HK == kHeadTc05 ? 4 : 1];
   __shared__ int32_t s_hact[HEAD ? GS_MAX_HEAD_TERMS : 1];
 
   __shared__ int32_t s_t[kDtThreads];   // the group's terms (one batch)
@@ -435,6 +462,22 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   // that starts at tile (b / ng) tiles_per_cta, for query group b % ng; the
   // group's data are read once and serve all of them.  Recovery passes: a
   // persistent grid walks the (overflowed group, tile run) units.
+  uint32_t tmem = 0, mbar_phase = 0;
+  bool tc_ok = true;
+  if constexpr (HK == kHeadTc05) {
+    if (warp == 0) {
+      tc05::alloc(&s_tmem, kTc05Cols);
+      tc05::relinquish();
+    }
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < 4; ++i) tc05::mbar_init(&s_mbar[i], 1);
+      tc05::mbar_init_fence();
+    }
+    tc05::fence_before();
+    __syncthreads();
+    tc05::fence_after();
+    tmem = s_tmem;
+  }
   int n_units = 1, unit0 = 0, ustep = 1, n_ovg = 1;
   if constexpr (MODE == kModeRecover) {
     n_ovg = (int)__ldcg(rec.n_groups);
@@ -527,6 +570,25 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           const uint32_t raw = __ldg(headw + ((int64_t)g * H + s_hact[i / kHeadG]) * kHeadG + (i % kHeadG));
           memcpy(&s_w[i], &raw, 4);
         }
+      if constexpr (HK == kHeadTc05) {
+        // B operands W_hi, W_lo [24 rows x 16 queries], K-major without swizzle:
+        // row a, query q at float (a / 4) * 64 + q * 4 + a % 4 (core matrices of
+        // 8 queries x 4 rows, 128 B); the tensor core reads TF32 (the 13 low
+        // mantissa bits ignored), so W_hi = W with those bits cleared and
+        // W_lo = W - W_hi carries the rest
+        float* whi = reinterpret_cast<float*>(s_af);
+        float* wlo = whi + kTc05MaxRows * kHeadG;
+        for (int i = threadIdx.x; i < kTc05MaxRows * kHeadG; i += blockDim.x) {
+          const int a = i / kHeadG, q = i % kHeadG;
+          float w = 0.f;
+          if (a < nact) w = __uint_as_float(__ldg(headw + ((int64_t)g * H + s_hact[a]) * kHeadG + q));
+          const float hi = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+          const int o = (a >> 2) * 64 + q * 4 + (a & 3);
+          whi[o] = hi;
+          wlo[o] = w - hi;
+        }
+        tc05::fence_proxy_async_smem();
+      }
       const int KS = HK == kHeadTensor ? (nact + 7) / 8 : 0;
       for (int i = threadIdx.x; i < KS * 32; i += blockDim.x) {
         const int ks = i >> 5, gid = (i & 31) >> 2, tig = i & 3;
@@ -764,7 +826,88 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         // dense head: S[q][d] += sum_a W[q][a] X[a][d] over the group's active
         // head rows a, a contraction of 16 queries x nact rows x T documents.
         const int ib = impact_bytes(IMPACT);
-        if (HK == kHeadFma) {
+        if constexpr (HK == kHeadTc05) {
+          // tensor-memory MMAs (FP32 impacts).  Warpgroup w takes the 128-document
+          // M-tiles w, w + 4, ...; thread (warp quarter r, lane l) owns document
+          // 32 r + l of the M-tile and tensor-memory lane 32 r + l.  Its head
+          // impacts X[a][d] (a < 24) go to columns A_hi (X with the 13 low
+          // mantissa bits ignored by the tensor core) and A_lo = X - X_hi; one
+          // thread per warpgroup issues D = A_hi W_hi + A_hi W_lo + A_lo W_hi
+          // (M = 128 documents, N = 16 queries, K = 8 rows per MMA); every
+          // thread then reads its document's 16 query sums and adds them to
+          // the tile rows.  The dropped A_lo W_lo term is below 2^-21 of |w x|.
+          const int wg = warp >> 2, wq = warp & 3;
+          const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+          const uint32_t c_ahi = tmem + (uint32_t)(wg * 64), c_alo = c_ahi + kTc05MaxRows, c_d = c_ahi + 48;
+          const int KP = (nact + 7) & ~7;
+          constexpr uint32_t kIdesc = tc05::instr_desc(1, 2, 2, 128, 16);
+          const float* whi = reinterpret_cast<const float*>(s_af);
+          const float* wlo = whi + kTc05MaxRows * kHeadG;
+          // the next M-tile's impacts are loaded while the current MMAs run
+          uint32_t xs[kTc05MaxRows];
+          auto load_x = [&](int mt) {
+            const float* xcol = reinterpret_cast<const float*>(head_dense) + doc0 + mt * 128 + wq * 32 + lane;
+#pragma unroll
+            for (int a = 0; a < kTc05MaxRows; ++a)
+              xs[a] = a < nact ? __float_as_uint(__ldg(xcol + (int64_t)s_hact[a] * head_ld)) : 0u;
+          };
+          const int n_mt = T / 128;
+          if (nact > 0 && wg < n_mt) load_x(wg);
+          if (nact > 0)
+            for (int mt = wg; mt < n_mt; mt += 4) {
+              const int dl = mt * 128 + wq * 32 + lane;
+#pragma unroll
+              for (int c = 0; c < kTc05MaxRows / 8; ++c) {
+                if (8 * c >= KP) break;
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  hi[j] = xs[8 * c + j];
+                  lo[j] = __float_as_uint(__uint_as_float(hi[j]) - __uint_as_float(hi[j] & 0xFFFFE000u));
+                }
+                tc05::st_x8(lane_base + c_ahi + 8 * c, hi);
+                tc05::st_x8(lane_base + c_alo + 8 * c, lo);
+              }
+              tc05::wait_st();
+              tc05::fence_before();
+              wg_barrier(wg);
+              if (wq == 0 && lane == 0) {
+                tc05::fence_after();
+                for (int s8 = 0; s8 < KP / 8; ++s8) {
+                  // rows 8 s8 .. 8 s8 + 7: two 16-byte core-matrix columns of B
+                  const uint64_t bh = tc05::smem_desc(whi + s8 * 128, 256, 128);
+                  const uint64_t bl = tc05::smem_desc(wlo + s8 * 128, 256, 128);
+                  tc05::mma_tf32_ts(c_d, c_ahi + 8 * s8, bh, kIdesc, s8 > 0);
+                  tc05::mma_tf32_ts(c_d, c_ahi + 8 * s8, bl, kIdesc, 1);
+                  tc05::mma_tf32_ts(c_d, c_alo + 8 * s8, bh, kIdesc, 1);
+                }
+                tc05::commit(&s_mbar[wg]);
+              }
+              if (mt + 4 < n_mt) load_x(mt + 4);
+              // bounded wait; on a timeout every warp still takes the same
+              // path (no barrier is left waiting) and the search reports it
+              const bool done = tc05::mbar_wait(&s_mbar[wg], mbar_phase, kTc05WaitTries);
+              mbar_phase ^= 1u;
+              tc_ok = tc_ok && done;
+              tc05::fence_after();
+              uint32_t dv[16];
+              tc05::ld_x16(lane_base + c_d, dv);
+              tc05::wait_ld();
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                if (q < gq) {
+                  AccT* cell = acc + q * T + dl;
+                  *cell = tail_value(*cell, fx, s_isc[q]) + __uint_as_float(dv[q]);
+                }
+              }
+              tc05::fence_before();
+            }
+          if (fx && nact == 0) {
+            // no head rows: fixed-point rows become floats
+            for (int i = threadIdx.x; i < gq * T; i += blockDim.x)
+              reinterpret_cast<float*>(acc)[i] = tail_value(reinterpret_cast<float*>(acc)[i], true, s_isc[i / T]);
+          }
+        } else if (HK == kHeadFma) {
           // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
           // documents 2 p, 2 p + 1 of each slab of kSlab documents,
           // p = 32 w + l: the head rows are read coalesced, four rows in
@@ -1106,6 +1249,21 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       }
     }
   }
+  if constexpr (HK == kHeadTc05) {
+    if (!tc_ok) {
+      // a wait gave up: report it and give the MMAs in flight a last bounded wait
+      if ((threadIdx.x & 127) == 0) {
+        atomicOr(flags, kFlagTimeout);
+        tc05::mbar_wait(&s_mbar[warp >> 2], mbar_phase ^ 1u, kTc05WaitTries);
+      }
+    }
+    tc05::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc05::fence_after();
+      tc05::dealloc(tmem, kTc05Cols);
+    }
+  }
 }
 
 // Candidates of the sample tiles (their scores sit in the sample rows).
@@ -1355,7 +1513,7 @@ gs_status tile_occupancy(const DtConfig& c, int* ctas) {
 
 template <int IMPACT, int HK>
 gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
-                         const DtPlan& p, const gs_search_opts* opts, cudaStream_t s) {
+                         const DtPlan& p, const gs_search_opts* opts, uint32_t* flags, cudaStream_t s) {
   const size_t smem = (size_t)c.G * c.T * 4 + kDynSmemFixed;
   auto ks = dt_tile_kernel<IMPACT, kModeSample, HK>;
   auto km = dt_tile_kernel<IMPACT, kModeMain, HK>;
@@ -1373,7 +1531,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
         ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
         c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
         p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, ms, c.n_sample,
-        p.fixp, p.qscale, DtRecover{});
+        p.fixp, p.qscale, DtRecover{}, flags);
     GS_LAUNCH_CHECK();
     record_stage(opts, 2, s);
     if (IMPACT == GS_IMPACT_U8)
@@ -1392,7 +1550,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
       ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
       c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
       p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, mm, c.nt,
-      p.fixp, p.qscale, DtRecover{});
+      p.fixp, p.qscale, DtRecover{}, flags);
   GS_LAUNCH_CHECK();
   record_stage(opts, 4, s);
   return GS_OK;
@@ -1408,7 +1566,7 @@ gs_status launch_tiles_h(const gs_index* ix, const int32_t* q_indptr, int B, int
 // The grid is persistent: with no marked query every CTA returns at once.
 template <int IMPACT, int HK>
 gs_status launch_recover_h(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k,
-                           const DtConfig& c, const DtPlan& p, cudaStream_t s) {
+                           const DtConfig& c, const DtPlan& p, uint32_t* flags, cudaStream_t s) {
   using ST = typename std::conditional<IMPACT == GS_IMPACT_U8, int32_t, float>::type;
   const size_t smem = (size_t)c.G * c.T * (IMPACT == GS_IMPACT_U8 ? 4 : 8) + kDynSmemFixed;
   int per_sm = 1;
@@ -1424,7 +1582,7 @@ gs_status launch_recover_h(const gs_index* ix, const int32_t* q_indptr, int B, i
         ix->blocks, ix->term_block, ix->seg, ix->num_tiles, ix->N, q_indptr, B, q_nnz, c.G, c.T, c.m, c.R, c.ng,
         c.n_sample, p.u_terms, p.u_ptr, p.n_u, p.ent, p.samp, c.sample_docs, p.theta, k, p.cand, p.cand_cnt, c.cap,
         p.tiebm, c.bm_words, ix->head_dense, ix->head_ld, c.H, p.headw, p.head_act, p.head_nact, tpc, c.nt,
-        p.fixp, p.qscale, rec);
+        p.fixp, p.qscale, rec, flags);
     GS_LAUNCH_CHECK();
     if (pass < 3) {
       dt_over_select_kernel<ST><<<B, 1024, 0, s>>>(p.q_over, p.ov_hist, p.ov_prefix, p.ov_need, p.ov_theta, pass, k);
@@ -1436,15 +1594,19 @@ gs_status launch_recover_h(const gs_index* ix, const int32_t* q_indptr, int B, i
 
 template <int IMPACT>
 gs_status launch_tiles(const gs_index* ix, const int32_t* q_indptr, int B, int32_t q_nnz, int k, const DtConfig& c,
-                       const DtPlan& p, const gs_search_opts* opts, cudaStream_t s, bool recover) {
-  if (recover) {
-    if (c.HK == kHeadFma) return launch_recover_h<IMPACT, kHeadFma>(ix, q_indptr, B, q_nnz, k, c, p, s);
-    if (c.HK == kHeadTensor) return launch_recover_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, s);
-    return launch_recover_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, s);
+                       const DtPlan& p, const gs_search_opts* opts, uint32_t* flags, cudaStream_t s, bool recover) {
+  auto go = [&](auto hk) {
+    constexpr int HK = decltype(hk)::value;
+    if (recover) return launch_recover_h<IMPACT, HK>(ix, q_indptr, B, q_nnz, k, c, p, flags, s);
+    return launch_tiles_h<IMPACT, HK>(ix, q_indptr, B, q_nnz, k, c, p, opts, flags, s);
+  };
+  if (c.HK == kHeadFma) return go(std::integral_constant<int, kHeadFma>{});
+  if (c.HK == kHeadTensor) return go(std::integral_constant<int, kHeadTensor>{});
+  if (c.HK == kHeadTc05) {
+    if constexpr (IMPACT == GS_IMPACT_F32) return go(std::integral_constant<int, kHeadTc05>{});
+    return GS_ERR_UNSUPPORTED;
   }
-  if (c.HK == kHeadFma) return launch_tiles_h<IMPACT, kHeadFma>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
-  if (c.HK == kHeadTensor) return launch_tiles_h<IMPACT, kHeadTensor>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
-  return launch_tiles_h<IMPACT, kHeadNone>(ix, q_indptr, B, q_nnz, k, c, p, opts, s);
+  return go(std::integral_constant<int, kHeadNone>{});
 }
 
 // ---- exact top-k of dense score rows ------------------------------------
@@ -1673,6 +1835,10 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
     constexpr int I = decltype(impact_tag)::value;
     if (c.HK == kHeadFma) return tile_occupancy<I, kHeadFma>(c, &ctas);
     if (c.HK == kHeadTensor) return tile_occupancy<I, kHeadTensor>(c, &ctas);
+    if (c.HK == kHeadTc05) {
+      if constexpr (I == GS_IMPACT_F32) return tile_occupancy<I, kHeadTc05>(c, &ctas);
+      return GS_ERR_UNSUPPORTED;
+    }
     return tile_occupancy<I, kHeadNone>(c, &ctas);
   };
   switch (ix->impact) {
@@ -1714,10 +1880,14 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   record_stage(opts, 1, s);
   auto tiles = [&](bool recover) {
     switch (ix->impact) {
-      case GS_IMPACT_F32: return launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
-      case GS_IMPACT_F16: return launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
-      case GS_IMPACT_BF16: return launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
-      default: return launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, s, recover);
+      case GS_IMPACT_F32:
+        return launch_tiles<GS_IMPACT_F32>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, flags, s, recover);
+      case GS_IMPACT_F16:
+        return launch_tiles<GS_IMPACT_F16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, flags, s, recover);
+      case GS_IMPACT_BF16:
+        return launch_tiles<GS_IMPACT_BF16>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, flags, s, recover);
+      default:
+        return launch_tiles<GS_IMPACT_U8>(ix, q_indptr, B, (int32_t)q_nnz, k, c, p, opts, flags, s, recover);
     }
   };
   st = tiles(false);

@@ -24,8 +24,14 @@ __host__ __device__ constexpr int block_bytes(int impact) { return 128 + 32 * im
 constexpr uint32_t kFlagBadTerm = GS_FLAG_BAD_TERM;
 constexpr uint32_t kFlagBadWeight = GS_FLAG_BAD_WEIGHT;
 constexpr uint32_t kFlagCandOverflow = GS_FLAG_CAND_OVERFLOW;
+constexpr uint32_t kFlagTimeout = GS_FLAG_TIMEOUT;
 // flags that report invalid query data (the informational overflow bit aside)
 constexpr uint32_t kDataFlags = GS_FLAG_BAD_TERM | GS_FLAG_BAD_WEIGHT | GS_FLAG_BAD_INDPTR;
+// the status a synchronous call returns for a flag word
+inline gs_status flags_status(uint32_t f) {
+  if (f & kFlagTimeout) return GS_ERR_TIMEOUT;
+  return (f & kDataFlags) ? GS_ERR_DATA : GS_OK;
+}
 
 }  // namespace gs
 

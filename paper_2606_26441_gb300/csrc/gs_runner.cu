@@ -273,7 +273,7 @@ extern "C" gs_status gs_runner_search(gs_runner* r, const int32_t* h_q_indptr, c
   // the search's flag word leads the workspace
   GS_CUDA_TRY(cudaMemcpyAsync(r->h_flags, r->ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaStreamSynchronize(s));
-  return (*r->h_flags & gs::kDataFlags) ? GS_ERR_DATA : GS_OK;
+  return gs::flags_status(*r->h_flags);
 }
 
 extern "C" gs_status gs_runner_plan(gs_runner* r, int32_t batch, int32_t k, gs_search_opts* out_opts,

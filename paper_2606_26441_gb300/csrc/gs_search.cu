@@ -469,7 +469,7 @@ extern "C" gs_status gs_search_host(const gs_index* ix, const int32_t* h_q_indpt
   uint32_t flags = 0;  // the flag word leads the workspace
   GS_CUDA_TRY(cudaMemcpyAsync(&flags, workspace, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA_TRY(cudaStreamSynchronize(s));
-  return (flags & kDataFlags) ? GS_ERR_DATA : GS_OK;
+  return flags_status(flags);
 }
 
 extern "C" gs_status gs_search_plan(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k,

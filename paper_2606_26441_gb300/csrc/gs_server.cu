@@ -211,8 +211,8 @@ void completer_loop(gs_server* S, Lane* L) {
       if (e != cudaSuccess) {
         gs::set_cuda_error(e);
         st = GS_ERR_CUDA;
-      } else if (*L->h_flags & gs::kDataFlags) {
-        st = GS_ERR_DATA;  // submit validates every query: not expected
+      } else if (gs::flags_status(*L->h_flags) != GS_OK) {
+        st = gs::flags_status(*L->h_flags);  // submit validates every query: not expected
       }
     }
     const auto now = Clock::now();

@@ -21,7 +21,7 @@ GS_ERR_UNSUPPORTED, GS_ERR_DATA, GS_ERR_TIMEOUT, GS_ERR_WORKSPACE = 4, 5, 6, 7
 IMPACTS = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3}
 ALGOS = {"auto": 0, "term_parallel": 1, "doc_tiled": 2, "doc_parallel": 3}
 GS_FLAG_BAD_TERM, GS_FLAG_BAD_WEIGHT, GS_FLAG_CAND_OVERFLOW = 1, 2, 4
-GS_FLAG_BAD_INDPTR = 16
+GS_FLAG_TIMEOUT, GS_FLAG_BAD_INDPTR = 8, 16
 GS_MAX_K = 2048
 GS_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -185,8 +185,9 @@ def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_
               stage_events=None) -> gs_search_opts:
     """gs_search_opts (0 = the library's default for each field).
 
-    algo: "auto", "term_parallel", "doc_tiled" or "doc_parallel"; use_head: 0 = auto (FMA head
-    for FP32 impacts, tensor-core head otherwise), 1 = FMA head, 2 = tensor-core head, -1 = none;
+    algo: "auto", "term_parallel", "doc_tiled" or "doc_parallel"; use_head: 0 = auto (FMA head for
+    FP32 impacts, warp-level tensor-core head otherwise), 1 = FMA head, 2 = warp-level tensor-core head (mma.sync),
+    3 = tensor-memory head (tcgen05, FP32 impacts), -1 = none;
     sample_stride 1 = no sample (every document a candidate).  stage_events: None or
     GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
     o = gs_search_opts()
