@@ -70,7 +70,7 @@ def cores() -> int:
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_dt_tile_kernel_docs8.8m_b500_top1000.md")
-KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh")
+KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh", "gs_tc05.cuh")
 
 
 def kernel_source_digest():
