@@ -1463,16 +1463,14 @@ __global__ void __launch_bounds__(1024) dt_over_select_kernel(const uint32_t* __
 
 constexpr size_t kDynSmemFixed = kEntCap * sizeof(uint2) + (kItemCap + kChunkCap) * sizeof(uint16_t);
 
-// Raises the dynamic shared-memory ceiling of both tile kernels of this
-// form, once per device: no attribute call is issued while a stream is
-// being captured for a graph.
 // Recovery passes keep 8-byte tail accumulators for float impacts.
 constexpr size_t rec_acc_bytes(int impact) { return impact == GS_IMPACT_U8 ? kDtMaxAccBytes : 2 * kDtMaxAccBytes; }
 
 // Raises the dynamic shared-memory ceiling of the tile kernels of this form
 // and records the recovery kernel's resident CTAs per SM (at its largest
-// tile), once per device: no attribute call is issued while a stream is
-// being captured for a graph.
+// tile), once per device.  Index builds call it (dt_prepare_device) for every
+// head kind of their impact type, so that no search, which a caller may
+// capture into a graph, makes the attribute calls.
 template <int IMPACT, int HK>
 gs_status tile_smem_attr(int* rec_per_sm = nullptr) {
   static std::mutex mu;
@@ -1831,6 +1829,24 @@ gs_status dense_topk(const gs_index* ix, const void* rows, int64_t ld, int32_t B
 namespace {
 
 }  // namespace
+
+gs_status dt_prepare_device(const gs_index* ix) {
+  auto all_heads = [](auto impact_tag) -> gs_status {
+    constexpr int I = decltype(impact_tag)::value;
+    gs_status st = tile_smem_attr<I, kHeadNone>();
+    if (st == GS_OK) st = tile_smem_attr<I, kHeadFma>();
+    if (st == GS_OK) st = tile_smem_attr<I, kHeadTensor>();
+    if constexpr (I == GS_IMPACT_F32)
+      if (st == GS_OK) st = tile_smem_attr<I, kHeadTc05>();
+    return st;
+  };
+  switch (ix->impact) {
+    case GS_IMPACT_F32: return all_heads(std::integral_constant<int, GS_IMPACT_F32>{});
+    case GS_IMPACT_F16: return all_heads(std::integral_constant<int, GS_IMPACT_F16>{});
+    case GS_IMPACT_BF16: return all_heads(std::integral_constant<int, GS_IMPACT_BF16>{});
+    default: return all_heads(std::integral_constant<int, GS_IMPACT_U8>{});
+  }
+}
 
 gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search_opts* opts, gs_plan_info* out) {
   DtConfig c;

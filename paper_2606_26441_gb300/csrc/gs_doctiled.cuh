@@ -17,6 +17,11 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
                     int32_t B, int64_t q_nnz, int32_t k, int32_t* out_ids, void* out_scores, void* ws,
                     size_t ws_bytes, uint32_t* flags, const gs_search_opts* opts, cudaStream_t s);
 
+// Raises the doc-tiled kernels' dynamic shared-memory ceilings for the index's
+// impact type on the current device (every head kind) and records the recovery
+// kernel's occupancy; idempotent.
+gs_status dt_prepare_device(const gs_index* ix);
+
 // Exact top-k of B dense score rows (row q at rows + q * ld, N scores, float
 // or int32 on the uint8 path) by a sampled threshold and one candidate pass;
 // rows whose candidates overflow are selected again over the whole row.  The

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "gs_doctiled.cuh"
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -524,6 +525,13 @@ extern "C" gs_status gs_index_build_ex(const int64_t* doc_indptr, const int32_t*
     return cuda_fail(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
   if (herr) return fail(GS_ERR_DATA);
+  // the doc-tiled kernels' shared-memory ceilings are raised here, once per
+  // device and form, so that no search (which a caller may capture into a
+  // graph) makes the attribute calls
+  if (ix->seg) {
+    const gs_status st = dt_prepare_device(ix);
+    if (st != GS_OK) return fail(st);
+  }
   *out = ix;
   return GS_OK;
 }

@@ -701,3 +701,42 @@ def test_sharded_merge_equals_unsharded():
                 rid, rsc, _ = full.ref.topk(qs.indptr, qs.terms, qs.weights, kk)
                 check.check_float(full.ref, qs.indptr, qs.terms, qs.weights, ids.cpu().numpy(), sc.cpu().numpy(),
                                   rid, rsc, docs.n)
+
+
+def test_graph_capture_as_first_search_of_a_process():
+    """A runner without autotuning captures its first search into a graph; in a fresh
+    process that is the first search at all, so every attribute the kernels need must
+    already be set when the index is built (no attribute call inside a capture)."""
+    import os
+    import subprocess
+    import sys
+    _dev()
+    code = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch, synth, oracle
+from oracle import check
+from paper_2606_26441_gb300 import gpusparse as gs
+dev = torch.device("cuda:0")
+docs = synth.docs(30_000, seed=13)
+qs = synth.queries(12, seed=13)
+for impact in ("u8", "f32"):
+    idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                            torch.from_numpy(docs.weights).to(dev), docs.vocab, impact)
+    r = gs.Runner(idx, max_batch=16, max_q_nnz=int(qs.nnz), max_k=50, autotune=False)
+    ids, sc = r.search(torch.from_numpy(qs.indptr.astype(np.int32)), torch.from_numpy(qs.terms),
+                       torch.from_numpy(qs.weights), 50)
+    ref = oracle.OracleIndex.from_batch(docs, impact)
+    rid, rsc, _ = ref.topk(qs.indptr, qs.terms, qs.weights, 50)
+    if impact == "u8":
+        check.check_u8(ids.numpy(), sc.numpy(), rid, rsc)
+    else:
+        check.check_float(ref, qs.indptr, qs.terms, qs.weights, ids.numpy(), sc.numpy(), rid, rsc, docs.n)
+    r.free()
+    idx.free()
+print("capture-first ok")
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, "-c", code, root], capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-3000:]
+    assert "capture-first ok" in p.stdout
