@@ -70,7 +70,7 @@ def cores() -> int:
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_dt_tile_kernel_docs8.8m_b500_top1000.md")
-KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh", "gs_tc05.cuh")
+KERNEL_SOURCES = ("gs_doctiled.cu", "gs_doctiled.cuh", "gs_internal.cuh", "gs_topk.cuh", "gs_tc05.cuh", "gs_order.cu")
 
 
 def kernel_source_digest():
@@ -240,12 +240,22 @@ def naive_stream_bytes(docs, qs, impact, df):
     return int(df[qs.terms].sum()) * (4 + BYTES_PER_IMPACT[impact]) + 8 * qs.n * docs.n
 
 
-def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
+def group_terms(qs, order, g0, G):
+    """Query terms of the group at positions [g0, g0 + G) of `order` (None: the caller's order)."""
+    if order is None:
+        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
+        return qs.terms[a:e]
+    rows = [qs.terms[int(qs.indptr[q]):int(qs.indptr[q + 1])] for q in order[g0:g0 + G]]
+    return np.concatenate(rows) if rows else qs.terms[:0]
+
+
+def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info, order=None):
     """Algorithmic bytes of the dominant kernel per launch.
 
     doc_tiled main pass : sum over groups of sum over the group's distinct terms
                           of the term's postings outside the sample tiles,
-                          times (4 + impact bytes);
+                          times (4 + impact bytes); the groups are those the
+                          search used (`order`: the regrouped batch);
     term_parallel scatter: sum over (query, term) of the term's postings times
                           (4 + impact bytes), plus 4 B per score-row element
                           (each row is updated in place once it is zeroed).
@@ -259,8 +269,7 @@ def algorithmic_bytes(plan, docs, qs, impact, algo, layout_info):
     main_df = df - layout_info["sample_df"]
     post = 0
     for g0 in range(0, qs.n, G):
-        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
-        u = np.unique(qs.terms[a:e])
+        u = np.unique(group_terms(qs, order, g0, G))
         post += int(main_df[u].sum())
     return post * b, {"postings": post}
 
@@ -283,7 +292,7 @@ def microbench_rates():
     return out
 
 
-def compute_work(plan, docs, qs, df, sample_df, head_terms):
+def compute_work(plan, docs, qs, df, sample_df, head_terms, order=None):
     """Work of the doc-tiled main pass that is not HBM traffic: shared-memory
     reductions of the sparse tail (one per (query, posting) of a non-head term
     outside the sample tiles) and FMAs of the dense head (16 queries x the
@@ -296,8 +305,7 @@ def compute_work(plan, docs, qs, df, sample_df, head_terms):
     tail = 0
     head_rows = 0
     for g0 in range(0, qs.n, G):
-        a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + G)])
-        t = qs.terms[a:e]
+        t = group_terms(qs, order, g0, G)
         in_head = np.isin(t, list(head)) if head else np.zeros(t.shape, bool)
         tail += int(main_df[t[~in_head]].sum())
         head_rows += len(np.unique(t[in_head]))
@@ -426,6 +434,9 @@ def run_gpu(args, w, docs, qs, world, rank, local):
         r = time_form(gs, torch, idx, q, k, algo, args.steps, args.warmup, dist, local,
                       sample_clocks=form == args.headline, opts_kw=kw)
         plan = idx.plan(q.batch, q.nnz, k, gs.make_opts(algo, **kw))
+        # the groups the doc-tiled search used (it regroups the batch by shared tail terms)
+        r["order"] = (gs.gs_search_query_order(idx, q, k, gs.make_opts(algo, **kw), r["ws"]).cpu().numpy()
+                      if algo == "doc_tiled" and plan.query_order else None)
         results[form] = (r, plan, idx)
 
     # headline
@@ -438,7 +449,7 @@ def run_gpu(args, w, docs, qs, world, rank, local):
                    "sample_topk", "scoring", "final_topk"]
     T, R, ns = plan.tile_docs, plan.sample_stride, plan.sample_tiles
     layout_info = {"df": df, "sample_df": sample_term_counts(docs, T, R, ns) if head_algo == "doc_tiled" else 0}
-    alg_bytes, extra = algorithmic_bytes(plan, docs, qs, head_imp, head_algo, layout_info)
+    alg_bytes, extra = algorithmic_bytes(plan, docs, qs, head_imp, head_algo, layout_info, r["order"])
     kern_ms = r["stage_ms"][3]
     peak, peak_src = load_peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
@@ -464,13 +475,16 @@ def run_gpu(args, w, docs, qs, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head_imp, "data": "synthetic",
         "config": workload_config(w, head_imp, head_algo),
         "plan": {"group_queries": plan.group_queries, "tile_docs": plan.tile_docs, "sample_stride": plan.sample_stride,
-                 "sample_tiles": plan.sample_tiles, "cand_capacity": int(plan.cand_capacity)},
+                 "sample_tiles": plan.sample_tiles, "cand_capacity": int(plan.cand_capacity),
+                 "query_order": "regrouped by shared tail terms" if r["order"] is not None else "caller's order"},
         "vs_plain_fp32": (value / plain["qps"]) if plain and (head_imp, head_algo) != ("f32", "term_parallel") else None,
         "forms": forms_out,
         "roofline": {"bound": "hbm", "kernel": "dt_tile_kernel (main pass)" if head_algo == "doc_tiled"
                      else "tp_scatter_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                      "traffic": recorded_traffic(w.name, args.headline), "algorithmic_bytes": alg_bytes,
+                     "algorithmic_bytes_caller_order": algorithmic_bytes(plan, docs, qs, head_imp, head_algo,
+                                                                         layout_info)[0],
                      "kernel_ms": kern_ms,
                      "postings_read": extra["postings"], "scatter_updates": updates,
                      "naive_stream_bytes": naive_stream_bytes(docs, qs, head_imp, df),
@@ -488,7 +502,7 @@ def run_gpu(args, w, docs, qs, world, rank, local):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
         rates = microbench_rates()
-        tail, head_flops = compute_work(plan, docs, qs, df, layout_info["sample_df"], st.head_terms)
+        tail, head_flops = compute_work(plan, docs, qs, df, layout_info["sample_df"], st.head_terms, r["order"])
         comp = {"sm_mhz": mhz, "sms": sms, "tail_reductions": tail,
                 "tail_reductions_per_s": tail / (kern_ms / 1e3), "head_flops": head_flops,
                 "head_tflops": head_flops / (kern_ms / 1e3) / 1e12,

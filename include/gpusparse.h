@@ -190,6 +190,17 @@ typedef struct {
                             FP32 impacts and heads of at most 24 rows only,
                             else GS_ERR_UNSUPPORTED), -1 = off */
   void* const* stage_events; /* NULL, or GS_NUM_STAGE_EVENTS cudaEvent_t */
+  int32_t query_order;   /* DOC_TILED, groups of 8 queries or more: 1 =
+                            regroup the batch (two groups or more) so that
+                            queries sharing long sparse-tail posting lists
+                            share a group (each tile segment of a shared term
+                            is then read once for all of them; results are
+                            written at each query's own row and are the same
+                            as in the caller's order); 0 = regroup only where
+                            the library's cost model predicts a gain (at least
+                            4 groups and batch x documents large enough:
+                            about 64 queries over 8.8M documents on GB300);
+                            -1 = keep the caller's order */
 } gs_search_opts;
 
 /* --- index --------------------------------------------------------------- */
@@ -293,11 +304,27 @@ typedef struct {
   int32_t head_terms;    /* DOC_TILED: dense head terms used (0: none) */
   int32_t ctas_per_sm;   /* DOC_TILED: resident CTAs per SM of the scoring
                             kernel (occupancy calculator) */
-  int64_t reserved[3];
+  int64_t query_order;   /* DOC_TILED: 1 = the batch is regrouped by shared
+                            tail terms (gs_search_opts.query_order) */
+  int64_t reserved[2];
 } gs_plan_info;
 
 gs_status gs_search_plan(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
                          const gs_search_opts* opts, gs_plan_info* out);
+
+/* The query groups of the last DOC_TILED gs_search that used `workspace` with
+ * the same index, batch, q_nnz, k and opts, when that search regrouped the
+ * batch (gs_plan_info.query_order = 1): writes out_perm[p] = the caller's
+ * query at position p of the regrouped batch, whose group g holds positions
+ * [g G, g G + G) (G = gs_plan_info.group_queries).  For performance accounting
+ * (the tiles' postings are read once per group and distinct term, Sec. 4.1,
+ * Sec. 8 future work 1).  out_perm: [batch] int32, device or page-locked host
+ * memory; the copy is asynchronous on `stream`, after the search.  Returns
+ * GS_ERR_UNSUPPORTED when these arguments do not regroup (another algorithm,
+ * groups of fewer than 8 queries, a single group, query_order = -1). */
+gs_status gs_search_query_order(const gs_index* index, int32_t batch, int64_t q_nnz, int32_t k,
+                                const gs_search_opts* opts, const void* workspace, size_t workspace_bytes,
+                                int32_t* out_perm, gs_stream_t stream);
 
 /* Merge of per-shard top-k lists (documents sharded across GPUs or across
  * indexes: each shard holds a contiguous range of document ids and returns

@@ -62,6 +62,7 @@ struct DtConfig {
   int64_t sample_docs = 0;
   int64_t cap = 0;
   int64_t bm_words = 0;
+  bool order = false;  // the batch is regrouped by shared tail terms (gs_order.cu)
 };
 
 gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts, DtConfig* c) {
@@ -108,6 +109,7 @@ gs_status dt_config(const gs_index* ix, int B, int k, const gs_search_opts* opts
   const int64_t n_round = (ix->N + 255) / 256 * 256;
   c->cap = R > 0 ? std::min<int64_t>(n_round, (4 * (int64_t)k * R + 4096 + 255) / 256 * 256) : n_round;
   c->bm_words = (ix->N + 31) / 32;
+  c->order = dt_order_used(B, c->G, ix->N, opts);
   return GS_OK;
 }
 
@@ -136,6 +138,10 @@ struct DtPlan {
   int32_t* head_nact; // [ng]
   int32_t* fixp;      // [ng] 1: fixed-point tail
   int32_t* qscale;    // [B] S_q of the fixed-point tail
+  int32_t* o_indptr;  // regrouped batch (c.order): query CSR [B + 1], [q_nnz], [q_nnz]
+  int32_t* o_terms;
+  float* o_w;
+  int32_t* perm;      // [B] the caller's query at each position of the regrouped batch
 };
 
 DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const DtConfig& c, size_t* bytes) {
@@ -165,6 +171,12 @@ DtPlan carve_dt(void* ws, const gs_index* ix, int B, int64_t q_nnz, int k, const
   p.head_nact = cv.take<int32_t>(c.ng);
   p.fixp = cv.take<int32_t>(c.ng);
   p.qscale = cv.take<int32_t>(B);
+  if (c.order) {
+    p.o_indptr = cv.take<int32_t>((size_t)B + 1);
+    p.o_terms = cv.take<int32_t>(q_nnz + 1);
+    p.o_w = cv.take<float>(q_nnz + 1);
+    p.perm = cv.take<int32_t>(B);
+  }
   *bytes = cv.size();
   return p;
 }
@@ -910,9 +922,10 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
         } else if (HK == kHeadFma) {
           // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
           // documents 2 p, 2 p + 1 of each slab of kSlab documents,
-          // p = 32 w + l: the head rows are read coalesced, four rows in
-          // flight, the weights are warp-wide broadcasts, and every (query,
-          // document) cell has one owner (no atomics)
+          // p = 32 w + l: the head rows are read coalesced, the next four rows
+          // loading while four are multiplied, the weights are warp-wide
+          // broadcasts, and every (query, document) cell has one owner (no
+          // atomics)
           constexpr int kSlab = 2 * kDtThreads;
           const int dp = warp * 32 + lane;
           for (int slab = 0; slab < T; slab += kSlab) {
@@ -940,12 +953,21 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                 x1 = (AccT)f.y;
               }
             };
+            // four head rows in registers, the next four already loading
+            AccT xn[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              xn[u][0] = xn[u][1] = (AccT)0;
+              if (u < nact) load2(u, xn[u][0], xn[u][1]);
+            }
             for (int a0 = 0; a0 < nact; a0 += 4) {
               AccT xs[4][2];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
-                xs[u][0] = xs[u][1] = (AccT)0;
-                if (a0 + u < nact) load2(a0 + u, xs[u][0], xs[u][1]);
+                xs[u][0] = xn[u][0];
+                xs[u][1] = xn[u][1];
+                xn[u][0] = xn[u][1] = (AccT)0;
+                if (a0 + 4 + u < nact) load2(a0 + 4 + u, xn[u][0], xn[u][1]);
               }
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
@@ -1326,7 +1348,8 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
                                                         const uint32_t* __restrict__ tiebm, int64_t bm_words,
                                                         int64_t N, const uint32_t* __restrict__ theta_bits, int R,
                                                         int k, int32_t* __restrict__ out_ids,
-                                                        ST* __restrict__ out_scores, uint32_t* flags, DtOverflow ov) {
+                                                        ST* __restrict__ out_scores, uint32_t* flags, DtOverflow ov,
+                                                        const int32_t* __restrict__ out_row) {
   __shared__ uint32_t hist[2048];
   __shared__ uint32_t ck[GS_MAX_K];
   __shared__ int32_t cid[GS_MAX_K];
@@ -1396,9 +1419,10 @@ __global__ void __launch_bounds__(1024) dt_final_kernel(const uint2* __restrict_
     cid[i] = 0x7fffffff;
   }
   bitonic_sort_desc(ck, cid, n_pad);
+  const int64_t orow = out_row ? (int64_t)__ldg(out_row + q) : (int64_t)q;  // the caller's row of this query
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    out_ids[(int64_t)q * k + j] = cid[j];
-    out_scores[(int64_t)q * k + j] = key_to_score<ST>(ck[j]);
+    out_ids[orow * k + j] = cid[j];
+    out_scores[orow * k + j] = key_to_score<ST>(ck[j]);
   }
 }
 
@@ -1804,7 +1828,7 @@ gs_status dense_topk(const gs_index* ix, const void* rows, int64_t ld, int32_t B
     GS_LAUNCH_CHECK();
     dt_final_kernel<int32_t, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
                                                        p.theta, c.R, k, out_ids, static_cast<int32_t*>(out_scores),
-                                                       flags, ov);
+                                                       flags, ov, nullptr);
     GS_LAUNCH_CHECK();
     topk_dense_rows_kernel<int32_t><<<B, kTopkThreads, 0, s>>>(static_cast<const int32_t*>(rows), ld, ix->N, k,
                                                               out_ids, static_cast<int32_t*>(out_scores), p.q_over);
@@ -1817,7 +1841,8 @@ gs_status dense_topk(const gs_index* ix, const void* rows, int64_t ld, int32_t B
                                                                    c.bm_words);
     GS_LAUNCH_CHECK();
     dt_final_kernel<float, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
-                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov);
+                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov,
+                                                     nullptr);
     GS_LAUNCH_CHECK();
     topk_dense_rows_kernel<float><<<B, kTopkThreads, 0, s>>>(static_cast<const float*>(rows), ld, ix->N, k,
                                                             out_ids, static_cast<float*>(out_scores), p.q_over);
@@ -1831,6 +1856,8 @@ namespace {
 }  // namespace
 
 gs_status dt_prepare_device(const gs_index* ix) {
+  const gs_status ost = dt_order_prepare_device();
+  if (ost != GS_OK) return ost;
   auto all_heads = [](auto impact_tag) -> gs_status {
     constexpr int I = decltype(impact_tag)::value;
     gs_status st = tile_smem_attr<I, kHeadNone>();
@@ -1861,6 +1888,7 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
   out->sample_tiles = c.n_sample;
   out->cand_capacity = c.cap;
   out->head_terms = c.H;
+  out->query_order = c.order ? 1 : 0;
   int ctas = 0;
   auto occ = [&](auto impact_tag) {
     constexpr int I = decltype(impact_tag)::value;
@@ -1883,6 +1911,19 @@ gs_status dt_plan_info(const gs_index* ix, int32_t B, int32_t k, const gs_search
   return GS_OK;
 }
 
+gs_status dt_order_of(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k, const gs_search_opts* opts,
+                      const void* ws, size_t ws_bytes, int32_t* out_perm, cudaStream_t s) {
+  DtConfig c;
+  gs_status st = dt_config(ix, B, k, opts, &c);
+  if (st != GS_OK) return st;
+  if (!c.order) return GS_ERR_UNSUPPORTED;
+  size_t need = 0;
+  const DtPlan p = carve_dt(const_cast<void*>(ws), ix, B, q_nnz, k, c, &need);
+  if (need > ws_bytes) return GS_ERR_WORKSPACE;
+  GS_CUDA_TRY(cudaMemcpyAsync(out_perm, p.perm, sizeof(int32_t) * (size_t)B, cudaMemcpyDefault, s));
+  return GS_OK;
+}
+
 gs_status dt_workspace_bytes(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k, const gs_search_opts* opts,
                              size_t* bytes) {
   DtConfig c;
@@ -1902,6 +1943,16 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   DtPlan p = carve_dt(ws, ix, B, q_nnz, k, c, &need);
   if (need > ws_bytes) return GS_ERR_WORKSPACE;
   record_stage(opts, 0, s);
+  if (c.order) {
+    // the rest of the search runs on the regrouped batch; results go to each query's own row
+    st = dt_order(ix, q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, c.H > 0 ? ix->head_slot : nullptr, p.o_indptr,
+                  p.o_terms, p.o_w, p.perm, s);
+    if (st != GS_OK) return st;
+    q_indptr = p.o_indptr;
+    q_terms = p.o_terms;
+    q_w = p.o_w;
+  }
+  const int32_t* out_row = c.order ? p.perm : nullptr;
   dt_prep_kernel<<<c.ng, 1024, 0, s>>>(q_indptr, q_terms, q_w, B, (int32_t)q_nnz, c.G, ix->V, ix->impact, p.cnt,
                                        p.u_terms, p.u_ptr, p.n_u, p.ent, ix->head_slot, c.H, p.headw, p.head_act,
                                        p.head_nact, ix->max_abs, p.fixp, p.qscale, flags);
@@ -1937,10 +1988,11 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
   if (ix->impact == GS_IMPACT_U8)
     dt_final_kernel<int32_t, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
                                                        p.theta, c.R, k, out_ids, static_cast<int32_t*>(out_scores),
-                                                       flags, ov);
+                                                       flags, ov, out_row);
   else
     dt_final_kernel<float, false><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N, p.theta,
-                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov);
+                                                     c.R, k, out_ids, static_cast<float*>(out_scores), flags, ov,
+                                                     out_row);
   GS_LAUNCH_CHECK();
   // Without a sample every document is a candidate (cap >= N): no list can
   // overflow.  With one, the queries the first final pass marked are
@@ -1951,11 +2003,11 @@ gs_status dt_search(const gs_index* ix, const int32_t* q_indptr, const int32_t* 
     if (ix->impact == GS_IMPACT_U8)
       dt_final_kernel<int32_t, true><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
                                                         p.ov_theta, 1, k, out_ids,
-                                                        static_cast<int32_t*>(out_scores), flags, ov);
+                                                        static_cast<int32_t*>(out_scores), flags, ov, out_row);
     else
       dt_final_kernel<float, true><<<B, 1024, 0, s>>>(p.cand, p.cand_cnt, c.cap, p.tiebm, c.bm_words, ix->N,
                                                       p.ov_theta, 1, k, out_ids, static_cast<float*>(out_scores),
-                                                      flags, ov);
+                                                      flags, ov, out_row);
     GS_LAUNCH_CHECK();
   }
   record_stage(opts, 5, s);

@@ -4,7 +4,8 @@
 // Batches are padded to power-of-two buckets (padding rows are empty
 // queries, whose results are never copied out).  The first batch of each
 // (bucket, k) is used to time a list of candidate doc-tiled plans — tile
-// length T, queries per group G, sample stride R, dense head on or off — the
+// length T, queries per group G, sample stride R, dense head on or off, batch
+// in the caller's order or regrouped by shared tail terms — the
 // grid-search analogue of the paper's BLOCK_PL tuning (Sec. 5.2); the fastest
 // plan's whole gs_search (prep, scoring, top-k) is captured once into a CUDA
 // graph and every later batch of that bucket replays it with one launch.
@@ -83,14 +84,18 @@ std::vector<gs_search_opts> candidates(const gs_index* ix, const gs_search_opts&
         // fixed at 16 queries, and it can pay even half-filled)
         if (G > bucket && G != 4 && head != 0) continue;
         for (int R : {32, 64, 128}) {
-          gs_search_opts o = base;
-          o.algo = GS_ALGO_DOC_TILED;
-          o.tile_docs = T;
-          o.group_queries = G;
-          o.use_head = head;
-          o.sample_stride = R;
-          o.stage_events = nullptr;
-          out.push_back(o);
+          for (int qo : {-1, 1}) {  // caller's order, or regrouped by shared tail terms
+            if (qo == 1 && (G < 8 || bucket < 2 * G)) continue;
+            gs_search_opts o = base;
+            o.algo = GS_ALGO_DOC_TILED;
+            o.tile_docs = T;
+            o.group_queries = G;
+            o.use_head = head;
+            o.sample_stride = R;
+            o.query_order = qo;
+            o.stage_events = nullptr;
+            out.push_back(o);
+          }
         }
       }
     }

@@ -486,6 +486,20 @@ extern "C" gs_status gs_search_plan(const gs_index* ix, int32_t B, int64_t q_nnz
   return GS_OK;
 }
 
+extern "C" gs_status gs_search_query_order(const gs_index* ix, int32_t B, int64_t q_nnz, int32_t k,
+                                           const gs_search_opts* opts, const void* workspace, size_t workspace_bytes,
+                                           int32_t* out_perm, gs_stream_t stream) {
+  gs_status st = check_query_args(ix, B, q_nnz, k, true);
+  if (st != GS_OK) return st;
+  if (!workspace || !out_perm) return GS_ERR_INVALID_ARG;
+  if (resolve_algo(ix, opts) != GS_ALGO_DOC_TILED) return GS_ERR_UNSUPPORTED;
+  size_t tp_bytes = 0;
+  carve_tp(nullptr, ix, B, q_nnz, false, &tp_bytes, k);
+  if (workspace_bytes < tp_bytes) return GS_ERR_WORKSPACE;
+  return dt_order_of(ix, B, q_nnz, k, opts, static_cast<const uint8_t*>(workspace) + tp_bytes,
+                     workspace_bytes - tp_bytes, out_perm, reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" gs_status gs_search_flags(const void* workspace, gs_stream_t stream, uint32_t* flags) {
   if (!workspace || !flags) return GS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -28,7 +28,8 @@ GS_STATIC_SCRATCH_BYTES = 64 << 20
 EXPORTED = (
     "gs_index_build", "gs_index_build_ex", "gs_index_info", "gs_index_get_layout", "gs_index_free",
     "gs_search_workspace_size", "gs_search", "gs_search_host", "gs_score_dense", "gs_search_flags",
-    "gs_search_plan", "gs_search_static", "gs_search_static_flags", "gs_runner_create", "gs_runner_search", "gs_runner_plan",
+    "gs_search_plan", "gs_search_query_order", "gs_search_static", "gs_search_static_flags", "gs_runner_create",
+    "gs_runner_search", "gs_runner_plan",
     "gs_runner_free", "gs_server_create", "gs_server_submit", "gs_server_wait", "gs_server_stats_get",
     "gs_server_destroy", "gs_merge_topk",
     "gs_status_str", "gs_last_cuda_error", "gs_version", "gs_kernel_launches",
@@ -69,7 +70,8 @@ class gs_index_layout(ctypes.Structure):
 class gs_search_opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("group_queries", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
                 ("chunk_blocks", ctypes.c_int32), ("sample_stride", ctypes.c_int32),
-                ("use_head", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p))]
+                ("use_head", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
+                ("query_order", ctypes.c_int32)]
 
 
 class gs_plan_info(ctypes.Structure):
@@ -77,7 +79,7 @@ class gs_plan_info(ctypes.Structure):
                 ("sample_stride", ctypes.c_int32), ("num_groups", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("sample_tiles", ctypes.c_int32), ("chunk_blocks", ctypes.c_int32),
                 ("cand_capacity", ctypes.c_int64), ("head_terms", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("query_order", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 class gs_server_config(ctypes.Structure):
@@ -152,6 +154,8 @@ def load(path: str = LIB_PATH):
     L.gs_merge_topk.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64), I32, I32, I32, I32, I32,
                                 P, P, P]
     L.gs_merge_topk.restype = ctypes.c_int
+    L.gs_search_query_order.argtypes = [P, I32, I64, I32, ctypes.POINTER(gs_search_opts), P, SZ, P, P]
+    L.gs_search_query_order.restype = ctypes.c_int
     L.gs_search_flags.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint32)]
     L.gs_search_flags.restype = ctypes.c_int
     L.gs_status_str.argtypes = [ctypes.c_int]
@@ -182,19 +186,22 @@ def _stream(stream):
 
 
 def make_opts(algo="auto", group_queries=0, tile_docs=0, chunk_blocks=0, sample_stride=0, use_head=0,
-              stage_events=None) -> gs_search_opts:
+              stage_events=None, query_order=0) -> gs_search_opts:
     """gs_search_opts (0 = the library's default for each field).
 
     algo: "auto", "term_parallel", "doc_tiled" or "doc_parallel"; use_head: 0 = auto (FMA head for
     FP32 impacts, warp-level tensor-core head otherwise), 1 = FMA head, 2 = warp-level tensor-core head (mma.sync),
     3 = tensor-memory head (tcgen05, FP32 impacts), -1 = none;
     sample_stride 1 = no sample (every document a candidate).  stage_events: None or
-    GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries)."""
+    GS_NUM_STAGE_EVENTS torch.cuda.Event objects (recorded at stage boundaries).  query_order: 1 = the
+    doc-tiled search regroups the batch by shared tail terms (results stay at each query's own row),
+    0 = regroup where the library's cost model predicts a gain, -1 = keep the caller's order."""
     o = gs_search_opts()
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.group_queries, o.tile_docs = group_queries, tile_docs
     o.chunk_blocks, o.sample_stride = chunk_blocks, sample_stride
     o.use_head = use_head
+    o.query_order = query_order
     if stage_events is not None:
         assert len(stage_events) == GS_NUM_STAGE_EVENTS
         arr = (ctypes.c_void_p * GS_NUM_STAGE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in stage_events])
@@ -381,6 +388,18 @@ def gs_search_static_flags(stream=None) -> int:
     return int(f.value)
 
 
+def gs_search_query_order(index: Index, q: Queries, k: int, opts, workspace: torch.Tensor, stream=None) -> torch.Tensor:
+    """The regrouped order of the last doc-tiled search on this workspace: perm[p] = the caller's query at
+    position p (group g = positions [g G, g G + G)).  Raises GsError(GS_ERR_UNSUPPORTED) when the search
+    did not regroup."""
+    L = load()
+    perm = torch.empty(q.batch, dtype=torch.int32, device=workspace.device)
+    _check(L.gs_search_query_order(index.handle, q.batch, q.nnz, k, ctypes.byref(opts) if opts else None,
+                                   _ptr(workspace), workspace.numel(), _ptr(perm), _stream(stream)),
+           "gs_search_query_order")
+    return perm
+
+
 def gs_search_flags(workspace: torch.Tensor, stream=None) -> int:
     """Synchronises the stream and returns the GS_FLAG_* bits of the last call on this workspace."""
     L = load()
@@ -419,7 +438,7 @@ class Runner:
         _check(self._L.gs_runner_plan(self._h, batch, k, ctypes.byref(o), ctypes.byref(ms)), "gs_runner_plan")
         return {"algo": o.algo, "tile_docs": o.tile_docs, "group_queries": o.group_queries,
                 "sample_stride": o.sample_stride, "use_head": o.use_head, "chunk_blocks": o.chunk_blocks,
-                "tuned_ms": ms.value}
+                "query_order": o.query_order, "tuned_ms": ms.value}
 
     def free(self):
         if self._h is not None and self._h.value:

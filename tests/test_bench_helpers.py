@@ -73,6 +73,18 @@ def test_byte_counts_against_direct_counts():
         a, e = int(qs.indptr[g0]), int(qs.indptr[min(qs.n, g0 + 8)])
         want += int(sum(main_df[t] for t in set(qs.terms[a:e].tolist())))
     assert extra["postings"] == want and got == want * (4 + 1)
+    # a regrouped batch: the groups are consecutive positions of the given order
+    order = np.random.default_rng(3).permutation(qs.n)
+    got_o, extra_o = bench.algorithmic_bytes(plan, docs, qs, "u8", "doc_tiled", {"df": df, "sample_df": sdf}, order)
+    want_o = 0
+    for g0 in range(0, qs.n, 8):
+        terms = set()
+        for q in order[g0:g0 + 8]:
+            terms.update(qs.row(int(q))[0].tolist())
+        want_o += int(sum(main_df[t] for t in terms))
+    assert extra_o["postings"] == want_o and got_o == want_o * (4 + 1)
+    ident = bench.algorithmic_bytes(plan, docs, qs, "u8", "doc_tiled", {"df": df, "sample_df": sdf}, np.arange(qs.n))
+    assert ident[0] == got
 
 
 def test_compute_work_against_direct_counts():

@@ -328,6 +328,33 @@ def test_fixed_point_tail_coarse_scale():
         c.idx.free()
 
 
+def test_thresholds_at_and_below_zero():
+    """Sampled thresholds theta_q <= 0: negative weights on the most frequent
+    terms (held by almost every document) make most scores negative, so the
+    top-k reaches the documents without those terms (score 0, ties at theta_q)
+    or negative scores.  The main pass keeps a document only if its own score
+    is >= theta_q, whatever the other documents of its chunk hold."""
+    gs = _gs()
+    docs = synth.docs(100_003, seed=11)
+    df = np.bincount(docs.terms, minlength=docs.vocab)
+    order = np.argsort(-df, kind="stable")
+    t0, t1, t2, t3 = (int(order[i]) for i in (0, 1, 2, 60))
+    rows = [([t0], [-1.0]), ([t0, t1], [-0.5, -0.25]), ([t0, t3], [-0.75, 2.0]), ([t1, t2, t3], [-1.0, -1.0, -0.5]),
+            ([t3], [-1.0]), ([], [])]
+    base = synth.queries(12, seed=11)
+    rows += [tuple(map(list, base.row(i))) for i in range(12)]
+    indptr = np.cumsum([0] + [len(r[0]) for r in rows]).astype(np.int64)
+    qs = synth.SparseBatch(indptr, np.array(sum([list(r[0]) for r in rows], []), np.int32),
+                           np.array(sum([list(r[1]) for r in rows], []), np.float32))
+    c = Case(docs, qs, "f32")
+    for kw in ({}, {"tile_docs": 2048}, {"use_head": 2}, {"use_head": -1}):
+        for k in (10, 1000, 2048):
+            plan = c.idx.plan(qs.n, qs.nnz, k, gs.make_opts("doc_tiled", **kw))
+            assert plan.sample_stride > 0  # the sampled-threshold main pass runs
+            c.check(k, "doc_tiled", **kw)
+    c.idx.free()
+
+
 @pytest.mark.parametrize("algo,kw", VARIANTS)
 @pytest.mark.parametrize("impact", ["f32", "f16", "bf16", "u8"])
 def test_handworked_golden_on_gpu(impact, algo, kw):
