@@ -770,15 +770,16 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           }
         };
         // units are claimed two at a time; both items' postings are loaded
-        // before either is scored, so that each warp keeps 256 postings in flight
+        // before either is scored, so that each warp keeps 256 postings in
+        // flight; the next claim's shared atomic is issued first and read at
+        // the end of the iteration, off the loads' critical path
         auto run_units = [&](auto fxc) {
-          int nxt = 0;
-          if (lane == 0) nxt = atomicAdd(&s_next, 2);
-          nxt = __shfl_sync(0xffffffffu, nxt, 0);
+          int nxt_raw = 0;
+          if (lane == 0) nxt_raw = atomicAdd(&s_next, 2);
+          int nxt = __shfl_sync(0xffffffffu, nxt_raw, 0);
           while (nxt < units) {
             const int it = nxt;
-            if (lane == 0) nxt = atomicAdd(&s_next, 2);
-            nxt = __shfl_sync(0xffffffffu, nxt, 0);
+            if (lane == 0) nxt_raw = atomicAdd(&s_next, 2);
             if (it + 1 < total) {
               int da[8];
               AccT x[8];
@@ -802,6 +803,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
                 }
               }
             }
+            nxt = __shfl_sync(0xffffffffu, nxt_raw, 0);
           }
         };
         if (fx) run_units(std::true_type{});
