@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
   __shared__ int32_t s_tb[kDtThreads];  // and their first index blocks
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t_shift = __ffs(T) - 1;  // T is a power of two: cell i lies in row i >> t_shift
   // Main and sample passes: CTA b scores the run of tiles_per_cta tiles
   // that starts at tile (b / ng) tiles_per_cta, for query group b % ng; the
   // group's data are read once and serve all of them.  Recovery passes: a
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
 #pragma unroll
           for (int j = 0; j < kPer; ++j) {
             const int i = c0 + j * kDtThreads + (int)threadIdx.x;
-            v[j] = i < n_cells && i / T < gq ? __ll2float_rn(a64[i]) * s_isc[i / T] : 0.f;
+            v[j] = i < n_cells && (i >> t_shift) < gq ? __ll2float_rn(a64[i]) * s_isc[i >> t_shift] : 0.f;
           }
           __syncthreads();
 #pragma unroll
@@ -919,7 +920,8 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
           if (fx && nact == 0) {
             // no head rows: fixed-point rows become floats
             for (int i = threadIdx.x; i < gq * T; i += blockDim.x)
-              reinterpret_cast<float*>(acc)[i] = tail_value(reinterpret_cast<float*>(acc)[i], true, s_isc[i / T]);
+              reinterpret_cast<float*>(acc)[i] =
+                  tail_value(reinterpret_cast<float*>(acc)[i], true, s_isc[i >> t_shift]);
           }
         } else if (HK == kHeadFma) {
           // CUDA-core FMAs.  Thread (warp w, lane l) owns the 16 queries and
@@ -1137,7 +1139,7 @@ __global__ void __launch_bounds__(kDtThreads, 2) dt_tile_kernel(
       } else if (fx) {
         // no head: fixed-point rows become floats
         float* af = reinterpret_cast<float*>(acc);
-        for (int i = threadIdx.x; i < gq * T; i += blockDim.x) af[i] = tail_value(af[i], true, s_isc[i / T]);
+        for (int i = threadIdx.x; i < gq * T; i += blockDim.x) af[i] = tail_value(af[i], true, s_isc[i >> t_shift]);
         __syncthreads();
       }
 
