@@ -104,6 +104,37 @@ def test_overflowed_queries_are_exact(coll, impact, use_head, k):
         idx.free()
 
 
+@pytest.mark.parametrize("impact", ["f32", "u8"])
+def test_overflow_recovery_on_a_regrouped_batch(coll, impact):
+    """The recovery passes work on the regrouped batch (query groups and the
+    recovery list in the regrouped order, results written at each query's own
+    row): regrouping puts the even queries, whose lists all overflow, together."""
+    gs = _gs()
+    dev = _dev()
+    docs, qs = coll
+    k = 100
+    idx = gs.gs_index_build(torch.from_numpy(docs.indptr).to(dev), torch.from_numpy(docs.terms).to(dev),
+                            torch.from_numpy(docs.weights).to(dev), docs.vocab, impact)
+    try:
+        q = gs.Queries.from_numpy(qs.indptr, qs.terms, qs.weights, dev)
+        opts = gs.make_opts("doc_tiled", query_order=1)
+        assert idx.plan(q.batch, q.nnz, k, opts).query_order == 1
+        ws = gs.alloc_workspace(idx, q.batch, q.nnz, k, opts)
+        ids, sc = gs.gs_search(idx, q, k, opts, ws)
+        assert gs.gs_search_flags(ws) == gs.GS_FLAG_CAND_OVERFLOW
+        perm = gs.gs_search_query_order(idx, q, k, opts, ws).cpu().numpy()
+        assert not np.array_equal(perm, np.arange(qs.n))  # the batch was regrouped
+        ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+        ref = oracle.OracleIndex.from_batch(docs, impact)
+        rid, rsc, _ = ref.topk(qs.indptr, qs.terms, qs.weights, k)
+        if impact == "u8":
+            check.check_u8(ids, sc, rid, rsc)
+        else:
+            check.check_float(ref, qs.indptr, qs.terms, qs.weights, ids, sc, rid, rsc, docs.n)
+    finally:
+        idx.free()
+
+
 def test_ordinary_batch_raises_no_overflow(coll):
     """The odd queries alone (their terms appear in the sample) do not overflow."""
     gs = _gs()
