@@ -572,25 +572,35 @@ def test_reduced_precision_error_vs_fp64():
 @pytest.mark.slow
 def test_full_size_batch_sampled_rows():
     """The bench's workload and launch: 8,841,823 documents, one batch of 500
-    queries, top-1000, default doc-tiled plan (groups of 16 queries).  The oracle
-    checks one returned row of every query group, at a different position in
-    each group (row 16 g + g mod the group's size), uint8 bit-exact and FP32 / FP16 / BF16
-    within tau."""
+    queries, top-1000, default doc-tiled plan (groups of 16 queries; at this size
+    the default regroups the batch by shared tail terms).  The oracle checks one
+    returned row of every query group the search used, at a different position in
+    each group (position 16 g + g mod the group's size of the regrouped batch),
+    uint8 bit-exact and FP32 / FP16 / BF16 within tau."""
     import os
+    gs = _gs()
     docs = synth.docs(synth.N_8_8M, seed=0, threads=os.cpu_count() or 0)
     qs = synth.queries(500, seed=0)
     k = 1000
-    rows = np.array([16 * g + g % min(16, qs.n - 16 * g) for g in range((qs.n + 15) // 16)])
-    assert len(rows) == 32 and rows[-1] < qs.n
-    parts = [qs.slice(int(r), int(r) + 1) for r in rows]
-    indptr = np.cumsum([0] + [p.nnz for p in parts]).astype(np.int64)
-    sample = synth.SparseBatch(indptr, np.concatenate([p.terms for p in parts]),
-                               np.concatenate([p.weights for p in parts]))
+    pos = np.array([16 * g + g % min(16, qs.n - 16 * g) for g in range((qs.n + 15) // 16)])
+    assert len(pos) == 32 and pos[-1] < qs.n
     for impact in ("u8", "f32", "f16", "bf16"):
         c = Case(docs, qs, impact)
-        ids, sc, flags = c.search(k, "doc_tiled")
-        assert flags == 0
+        opts = gs.make_opts("doc_tiled")
+        assert c.idx.plan(qs.n, qs.nnz, k, opts).query_order == 1
+        ws = gs.alloc_workspace(c.idx, c.q.batch, c.q.nnz, k, opts)
+        ids, sc = gs.gs_search(c.idx, c.q, k, opts, ws)
+        assert gs.gs_search_flags(ws) == 0
+        perm = gs.gs_search_query_order(c.idx, c.q, k, opts, ws).cpu().numpy()
+        assert np.array_equal(np.sort(perm), np.arange(qs.n))
+        ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+        del ws
         c.idx.free()
+        rows = perm[pos]  # the caller's queries at those positions of the regrouped batch
+        parts = [qs.slice(int(r), int(r) + 1) for r in rows]
+        indptr = np.cumsum([0] + [p.nnz for p in parts]).astype(np.int64)
+        sample = synth.SparseBatch(indptr, np.concatenate([p.terms for p in parts]),
+                                   np.concatenate([p.weights for p in parts]))
         rid, rsc, _ = c.ref.topk(sample.indptr, sample.terms, sample.weights, k)
         if impact == "u8":
             check.check_u8(ids[rows], sc[rows], rid, rsc)
